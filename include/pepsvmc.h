@@ -1,0 +1,147 @@
+/*
+ * pepsvmc -- C ABI of the per-sample single-layer PEPS contraction used by
+ * variational Monte Carlo (Liu, Huang, Gong, Gu, arXiv:1908.09359).
+ *
+ * One context holds, on one CUDA device, the PEPS tensors of an open Ly x Lx
+ * spin-1/2 lattice and n_chains Markov chains.  All arithmetic of the hot path
+ * runs in the library's own CUDA kernels on the stream given at init.
+ *
+ * Conventions shared by every call
+ *   - Return value: PEPSVMC_OK (0) or a negative PEPSVMC_E* code; the text of
+ *     the last error is available from pepsvmc_last_error().
+ *   - Host buffers are owned by the caller and only read or written during the
+ *     call.  Device memory is owned by the context and freed by
+ *     pepsvmc_destroy().  Calls that return host data synchronise the stream.
+ *   - Tensor layout ("packed"): sites in row-major lattice order (row k = 0 at
+ *     the top, column m = 0 at the left); each site is A(s, l, r, u, d) in
+ *     row-major order (Sec. II A, Eq. (1)) with s = 0 for spin +1 and s = 1
+ *     for spin -1; a leg on the open edge has dimension 1, every other leg D.
+ *   - Spins: int8 +1/-1, layout [chain][k][m].
+ *   - A context is not thread-safe; calls on one context must not overlap.
+ */
+#ifndef PEPSVMC_H
+#define PEPSVMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PEPSVMC_OK = 0,
+  PEPSVMC_EINVAL = -1,      /* bad argument or configuration                 */
+  PEPSVMC_ENOMEM = -2,      /* device or host allocation failed              */
+  PEPSVMC_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed   */
+  PEPSVMC_ETIMEOUT = -4,    /* a device-side wait exceeded its budget        */
+  PEPSVMC_ENONFINITE = -5,  /* a non-finite amplitude ratio, E_loc or log    */
+  PEPSVMC_EZEROPSI = -6,    /* a configuration with Psi(S) = 0 was met       */
+  PEPSVMC_ESTATE = -7       /* call out of order (e.g. no measurement yet)   */
+};
+
+enum { PEPSVMC_FP32 = 0, PEPSVMC_MIXED_BF16 = 1 };
+
+typedef struct pepsvmc_ctx pepsvmc_ctx;
+
+typedef struct {
+  int32_t Ly, Lx;       /* lattice rows and columns (>= 1 each, Ly*Lx even)  */
+  int32_t D;            /* virtual bond dimension (1..16)                   */
+  int32_t chi;          /* boundary-MPS cutoff Dc (App. B), 1..64           */
+  int32_t n_chains;     /* Markov chains advanced together (>= 1)          */
+  int32_t n_fit;        /* one-site fit half-sweeps per truncation, odd    */
+  double J1, J2;        /* NN and NNN couplings; J2 = 0 is Heisenberg      */
+  uint64_t seed;        /* Philox key for Metropolis and sign-SGD uniforms */
+  int32_t precision;    /* PEPSVMC_FP32 or PEPSVMC_MIXED_BF16              */
+  int32_t reserved[7];  /* must be zero                                    */
+} pepsvmc_config;
+
+/* Create a context.  Boundary-MPS truncation (App. B) is the variational fit
+ * of ||M|U> - |U'>||^2 by n_fit one-site half-sweeps; its starting guess is the
+ * random MPS ``sketch``.
+ *   tensors: host, packed layout above, float64, copied.
+ *   sketch:  host float64 array [max(Ly,Lx)][chi][D][chi] of iid N(0,1)
+ *            entries, copied.
+ *   stream:  a cudaStream_t (NULL = the legacy default stream).
+ * All chains start in the Neel configuration; use pepsvmc_set_spins to change.
+ * Errors: EINVAL (bad config), ENOMEM, ECUDA.                               */
+int pepsvmc_init(const pepsvmc_config* cfg, const double* tensors, const double* sketch,
+                 void* stream, pepsvmc_ctx** out);
+
+void pepsvmc_destroy(pepsvmc_ctx* ctx);
+const char* pepsvmc_last_error(const pepsvmc_ctx* ctx);
+
+/* Number of float64 entries of the packed tensor array (both spin slots). */
+int64_t pepsvmc_n_params(const pepsvmc_ctx* ctx);
+
+int pepsvmc_set_spins(pepsvmc_ctx* ctx, const int8_t* spins);  /* host, n_chains*Ly*Lx */
+int pepsvmc_get_spins(pepsvmc_ctx* ctx, int8_t* spins);
+int pepsvmc_set_tensors(pepsvmc_ctx* ctx, const double* tensors);
+int pepsvmc_get_tensors(pepsvmc_ctx* ctx, double* tensors);
+
+/* Sweep counter used in the Metropolis Philox counter (chain, sweep, bond, tag). */
+int pepsvmc_set_sweep_counter(pepsvmc_ctx* ctx, uint64_t sweep);
+uint64_t pepsvmc_get_sweep_counter(const pepsvmc_ctx* ctx);
+
+/* n_sweeps sequential Metropolis sweeps of every chain (Sec. II A, Eq. (9)):
+ * each sweep visits all vertical bonds (columns left to right, bonds top to
+ * bottom), then all horizontal bonds (rows top to bottom, bonds left to
+ * right), proposing a swap of every antiparallel pair and accepting it when
+ * r < min(1, |Psi(S_b)/Psi(S_a)|^2), r = Philox uniform.  Bond ids: vertical
+ * (k,m)-(k+1,m) is m*(Ly-1)+k, horizontal (k,m)-(k,m+1) is Lx*(Ly-1)+k*(Lx-1)+m.
+ *   accept_rate_out: nullable host double, accepted / proposed over the call.
+ * Errors: EZEROPSI, ENONFINITE, ECUDA.                                      */
+int pepsvmc_sample_sweep(pepsvmc_ctx* ctx, int32_t n_sweeps, double* accept_rate_out);
+
+/* Per-proposal record of the most recent sweep (after pepsvmc_enable_trace(ctx,1)):
+ *   ratio:    host float64 [n_chains][2*Lx*Ly - Lx - Ly], Psi(S_b)/Psi(S_a)
+ *   decision: host int8 same shape: -1 no proposal (parallel pair), 0 rejected,
+ *             1 accepted.  Both nullable.                                    */
+int pepsvmc_enable_trace(pepsvmc_ctx* ctx, int32_t on);
+int pepsvmc_get_trace(pepsvmc_ctx* ctx, double* ratio, int8_t* decision);
+
+/* Measure the current configurations (App. C; Eqs. (3)-(7)):
+ *   eloc:   E_loc(S) = sum over NN and NNN bonds of J s_i s_j / 4 plus, for
+ *           antiparallel pairs, (J/2) Psi(S')/Psi(S); horizontal ratios from
+ *           the three-line environments of each row, vertical and diagonal
+ *           ratios from four-line environments of each row pair.
+ *   logpsi, sign: ln|Psi(S)| and its sign from the contraction of row Ly/2.
+ *   All nullable, host, n_chains entries.  G(S) = Delta(S)/Psi(S) of every
+ *   chain is kept on the device for pepsvmc_get_chain_grad.
+ * Errors: EZEROPSI, ENONFINITE, ECUDA.                                      */
+int pepsvmc_measure(pepsvmc_ctx* ctx, double* eloc, double* logpsi, int8_t* sign);
+
+/* G(S) of one chain from the last measurement: host float64, packed layout of
+ * ONE spin slot per site, i.e. sum over sites of Dl*Dr*Du*Dd entries, each
+ * site (l, r, u, d) row-major; it belongs to slot s(k,m) of that chain.     */
+int64_t pepsvmc_n_grad_entries(const pepsvmc_ctx* ctx);
+int pepsvmc_get_chain_grad(pepsvmc_ctx* ctx, int32_t chain, double* out);
+
+/* Ln|Psi| and sign of the current configurations contracted at row ``row``
+ * (<B_row| M_row |T_row>, App. B), host arrays of n_chains, nullable.       */
+int pepsvmc_amplitude(pepsvmc_ctx* ctx, int32_t row, double* logpsi, int8_t* sign);
+
+/* Algorithm 1: n_sweeps times (one sweep of every chain, then a measurement),
+ * accumulating E_tot, P1 = sum G E_loc and P2 = sum G over all chains and
+ * sweeps in float64.  Outputs (host, nullable):
+ *   E_mean, E_var:   mean and variance of E_loc over the n_sweeps*n_chains samples
+ *   eloc, logpsi, sign: per sample [sweep][chain]
+ *   grad:            dE/dA = <G E_loc> - <G><E_loc> (Eq. (5), without the
+ *                    factor 2 of the exact derivative), packed layout.
+ * Errors: as pepsvmc_sample_sweep and pepsvmc_measure.                       */
+int pepsvmc_energy_and_grad(pepsvmc_ctx* ctx, int32_t n_sweeps, double* E_mean, double* E_var,
+                            double* eloc, double* logpsi, int8_t* sign, double* grad);
+
+/* Sign-SGD (Sec. II B, Eq. (10)) with the gradient of the last
+ * pepsvmc_energy_and_grad: A <- A - r * delta * sgn(dE/dA), r = Philox uniform
+ * with counter (element & 0xffffffff, element >> 32, step, tag).
+ * Errors: ESTATE if no gradient was computed.                               */
+int pepsvmc_update(pepsvmc_ctx* ctx, double delta, uint64_t step);
+
+/* Kernel launches issued by this context since its creation (a counter kept by
+ * the host side of the library). */
+int64_t pepsvmc_launch_count(const pepsvmc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEPSVMC_H */

@@ -333,6 +333,7 @@ def measure(grid, spins, chi, W, n_fit, J1, J2, Ts=None, logT=None, want_grad=Tr
         Ts, logT = top_envs(grid, spins, chi, W, n_fit)
     Bs, logB = bottom_envs(grid, spins, chi, W, n_fit)
     e = 0.0
+    scale = [0.0]   # sum of |terms| of E_loc (tolerance scale for comparisons)
     G = [[None] * Lx for _ in range(Ly)]
     logpsi = sign = None
     for k in range(Ly):
@@ -360,13 +361,16 @@ def measure(grid, spins, chi, W, n_fit, J1, J2, Ts=None, logT=None, want_grad=Tr
             if m < Lx - 1:
                 sg = spins[k, m] * spins[k, m + 1]
                 e += J1 * sg / 4.0
+                scale[0] += abs(J1) / 4.0
                 if sg < 0:
                     flip = env3_left(E, T[m], grid[k][m][1 - s], B[m])
-                    e += 0.5 * J1 * float(np.vdot(flip, Rf[m + 1]) / np.vdot(cur, R[m + 1]))
+                    t = 0.5 * J1 * float(np.vdot(flip, Rf[m + 1]) / np.vdot(cur, R[m + 1]))
+                    e += t
+                    scale[0] += abs(t)
             E, _ = _normalised(cur)
     for k in range(Ly - 1):
-        e += _pair_terms(grid, spins, k, Ts[k], Bs[k + 1], J1, J2)
-    return dict(eloc=e, logpsi=logpsi, sign=sign, G=G if want_grad else None)
+        e += _pair_terms(grid, spins, k, Ts[k], Bs[k + 1], J1, J2, scale)
+    return dict(eloc=e, logpsi=logpsi, sign=sign, G=G if want_grad else None, eloc_scale=scale[0])
 
 
 def _col(grid, spins, k, m, flip_top=False, flip_bot=False):
@@ -374,7 +378,7 @@ def _col(grid, spins, k, m, flip_top=False, flip_bot=False):
     return grid[k][m][1 - s1 if flip_top else s1], grid[k + 1][m][1 - s2 if flip_bot else s2]
 
 
-def _pair_terms(grid, spins, k, T, B, J1, J2):
+def _pair_terms(grid, spins, k, T, B, J1, J2, scale):
     """Vertical NN terms (k,m)-(k+1,m) and both NNN diagonals of rows (k, k+1)."""
     Lx = spins.shape[1]
     R4 = [None] * (Lx + 1)
@@ -389,26 +393,35 @@ def _pair_terms(grid, spins, k, T, B, J1, J2):
         den1 = np.vdot(cur, R4[m + 1])
         sg = spins[k, m] * spins[k + 1, m]
         e += J1 * sg / 4.0
+        scale[0] += abs(J1) / 4.0
         if sg < 0:
             fl = env4_left(E, T[m], *_col(grid, spins, k, m, True, True), B[m])
-            e += 0.5 * J1 * float(np.vdot(fl, R4[m + 1]) / den1)
+            t = 0.5 * J1 * float(np.vdot(fl, R4[m + 1]) / den1)
+            e += t
+            scale[0] += abs(t)
         if J2 != 0.0 and m < Lx - 1:
             nxt = env4_left(cur, T[m + 1], *_col(grid, spins, k, m + 1), B[m + 1])
             den2 = np.vdot(nxt, R4[m + 2])
             # diagonal (k,m)-(k+1,m+1)
             sg = spins[k, m] * spins[k + 1, m + 1]
             e += J2 * sg / 4.0
+            scale[0] += abs(J2) / 4.0
             if sg < 0:
                 f = env4_left(E, T[m], *_col(grid, spins, k, m, True, False), B[m])
                 f = env4_left(f, T[m + 1], *_col(grid, spins, k, m + 1, False, True), B[m + 1])
-                e += 0.5 * J2 * float(np.vdot(f, R4[m + 2]) / den2)
+                t = 0.5 * J2 * float(np.vdot(f, R4[m + 2]) / den2)
+                e += t
+                scale[0] += abs(t)
             # anti-diagonal (k,m+1)-(k+1,m)
             sg = spins[k, m + 1] * spins[k + 1, m]
             e += J2 * sg / 4.0
+            scale[0] += abs(J2) / 4.0
             if sg < 0:
                 f = env4_left(E, T[m], *_col(grid, spins, k, m, False, True), B[m])
                 f = env4_left(f, T[m + 1], *_col(grid, spins, k, m + 1, True, False), B[m + 1])
-                e += 0.5 * J2 * float(np.vdot(f, R4[m + 2]) / den2)
+                t = 0.5 * J2 * float(np.vdot(f, R4[m + 2]) / den2)
+                e += t
+                scale[0] += abs(t)
         E, _ = _normalised(cur)
     return e
 

@@ -1,0 +1,161 @@
+"""Python binding of the pepsvmc C ABI: argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; this module copies
+numpy arrays in and out and passes torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import FP32, MIXED_BF16, PepsvmcError  # noqa: F401
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _i8(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int8)) if a is not None else None
+
+
+class PepsVMC:
+    """One pepsvmc context (one device, n_chains Markov chains).
+
+    ``tensors``: float64 packed PEPS (see include/pepsvmc.h), ``sketch``: float64
+    (max(Ly,Lx), chi, D, chi) starting guess of the truncation fit.
+    """
+
+    def __init__(self, Ly, Lx, D, chi, n_chains, tensors, sketch, J1=1.0, J2=0.0, seed=0, n_fit=3,
+                 precision=FP32, stream=None):
+        self.lib = _lib.load()
+        cfg = _lib.Config()
+        cfg.Ly, cfg.Lx, cfg.D, cfg.chi, cfg.n_chains, cfg.n_fit = Ly, Lx, D, chi, n_chains, n_fit
+        cfg.J1, cfg.J2, cfg.seed, cfg.precision = float(J1), float(J2), int(seed), int(precision)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.shape = (n_chains, Ly, Lx)
+        self.n_chains, self.Ly, self.Lx = n_chains, Ly, Lx
+        t = np.ascontiguousarray(tensors, dtype=np.float64)
+        s = np.ascontiguousarray(sketch, dtype=np.float64)
+        if s.shape != (max(Ly, Lx), chi, D, chi):
+            raise ValueError(f"sketch must have shape {(max(Ly, Lx), chi, D, chi)}")
+        self.ctx = C.c_void_p()
+        rc = self.lib.pepsvmc_init(C.byref(cfg), _dp(t), _dp(s), C.c_void_p(stream), C.byref(self.ctx))
+        if rc != 0:
+            msg = self.lib.pepsvmc_last_error(self.ctx).decode() if self.ctx else ""
+            if self.ctx:
+                self.lib.pepsvmc_destroy(self.ctx)
+                self.ctx = None
+            raise PepsvmcError(rc, msg)
+        if t.size != self.n_params:
+            self.close()
+            raise ValueError(f"tensors must have {self.n_params} entries, got {t.size}")
+
+    # ----------------------------------------------------------------- plumbing
+    def _check(self, rc):
+        if rc != 0:
+            raise PepsvmcError(rc, self.lib.pepsvmc_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.pepsvmc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_params(self):
+        return int(self.lib.pepsvmc_n_params(self.ctx))
+
+    @property
+    def n_grad_entries(self):
+        return int(self.lib.pepsvmc_n_grad_entries(self.ctx))
+
+    @property
+    def launches(self):
+        return int(self.lib.pepsvmc_launch_count(self.ctx))
+
+    @property
+    def n_bonds(self):
+        return 2 * self.Lx * self.Ly - self.Lx - self.Ly
+
+    # ----------------------------------------------------------------- state
+    def set_spins(self, spins):
+        s = np.ascontiguousarray(spins, dtype=np.int8).reshape(self.shape)
+        self._check(self.lib.pepsvmc_set_spins(self.ctx, _i8(s)))
+
+    def get_spins(self):
+        s = np.empty(self.shape, dtype=np.int8)
+        self._check(self.lib.pepsvmc_get_spins(self.ctx, _i8(s)))
+        return s
+
+    def set_tensors(self, t):
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        self._check(self.lib.pepsvmc_set_tensors(self.ctx, _dp(t)))
+
+    def get_tensors(self):
+        t = np.empty(self.n_params, dtype=np.float64)
+        self._check(self.lib.pepsvmc_get_tensors(self.ctx, _dp(t)))
+        return t
+
+    def set_sweep_counter(self, n):
+        self._check(self.lib.pepsvmc_set_sweep_counter(self.ctx, int(n)))
+
+    @property
+    def sweep_counter(self):
+        return int(self.lib.pepsvmc_get_sweep_counter(self.ctx))
+
+    # ----------------------------------------------------------------- hot path
+    def sample_sweep(self, n_sweeps=1):
+        r = C.c_double()
+        self._check(self.lib.pepsvmc_sample_sweep(self.ctx, int(n_sweeps), C.byref(r)))
+        return r.value
+
+    def enable_trace(self, on=True):
+        self._check(self.lib.pepsvmc_enable_trace(self.ctx, 1 if on else 0))
+
+    def get_trace(self):
+        ratio = np.empty((self.n_chains, self.n_bonds), dtype=np.float64)
+        dec = np.empty((self.n_chains, self.n_bonds), dtype=np.int8)
+        self._check(self.lib.pepsvmc_get_trace(self.ctx, _dp(ratio), _i8(dec)))
+        return ratio, dec
+
+    def measure(self):
+        e = np.empty(self.n_chains)
+        lp = np.empty(self.n_chains)
+        sg = np.empty(self.n_chains, dtype=np.int8)
+        self._check(self.lib.pepsvmc_measure(self.ctx, _dp(e), _dp(lp), _i8(sg)))
+        return e, lp, sg
+
+    def chain_grad(self, chain):
+        g = np.empty(self.n_grad_entries)
+        self._check(self.lib.pepsvmc_get_chain_grad(self.ctx, int(chain), _dp(g)))
+        return g
+
+    def amplitude(self, row):
+        lp = np.empty(self.n_chains)
+        sg = np.empty(self.n_chains, dtype=np.int8)
+        self._check(self.lib.pepsvmc_amplitude(self.ctx, int(row), _dp(lp), _i8(sg)))
+        return lp, sg
+
+    def energy_and_grad(self, n_sweeps, want_samples=True, want_grad=True):
+        Em, Ev = C.c_double(), C.c_double()
+        n = int(n_sweeps) * self.n_chains
+        el = np.empty(n) if want_samples else None
+        lp = np.empty(n) if want_samples else None
+        sg = np.empty(n, dtype=np.int8) if want_samples else None
+        gr = np.empty(self.n_params) if want_grad else None
+        self._check(self.lib.pepsvmc_energy_and_grad(self.ctx, int(n_sweeps), C.byref(Em), C.byref(Ev),
+                                                     _dp(el), _dp(lp), _i8(sg), _dp(gr)))
+        return dict(E_mean=Em.value, E_var=Ev.value, eloc=el, logpsi=lp, sign=sg, grad=gr)
+
+    def update(self, delta, step):
+        self._check(self.lib.pepsvmc_update(self.ctx, float(delta), int(step)))

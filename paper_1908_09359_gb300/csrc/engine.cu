@@ -1,0 +1,1264 @@
+// Host engine and C ABI of the VMC-PEPS hot path (arXiv:1908.09359).
+//
+// The engine issues the device work of one context on one CUDA stream.  All
+// chains advance in lock step: every contraction is one batched launch over
+// the chains, and per-chain choices (the spin of a site, accept/reject) are
+// data on the device, never host branches.
+//
+// Lattice orientations.  Everything is written for rows swept top-down (the
+// boundary-MPS scheme of App. B); the other directions reuse it on re-oriented
+// lattices: O1 = upside down (bottom environments), O2 = transposed (columns,
+// for vertical bonds), O3 = transposed and upside down.  Each orientation has
+// its own permuted float copies of the site tensors.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "pepsvmc.h"
+
+using namespace pv;
+
+namespace {
+
+struct Orient {
+  int Ly, Lx;       // rows and columns in this orientation
+  bool tr, vf;      // transposed, upside down
+};
+
+// One site tensor of an oriented row: both spin slots, two permuted layouts.
+struct SiteOp {
+  const float* lurd;  // [(l,u)][(r,d)], slot 1 at +size
+  const float* urld;  // [(u,r)][(l,d)]
+  long long size;
+  int Dl, Dr, Du, Dd;
+  int spin;           // original lattice index k*Lx + m (selects the slot per chain)
+};
+
+// One boundary MPS for all chains: site m of chain c at base + m*site_stride + c*chain_stride.
+struct View {
+  const float* base;
+  long long site_stride, chain_stride;
+  const std::vector<int>* bond;  // L+1 bond dimensions
+  const double* logs;            // per chain log of the norm factored out
+  const float* site(int m) const { return base + (long long)m * site_stride; }
+};
+
+struct Store {
+  float* base = nullptr;
+  double* logs = nullptr;  // [rows][C]
+  int rows = 0, L = 0;
+  std::vector<std::vector<int>> bond;
+  float* row_ptr(int r, long long C, long long S) const { return base + (long long)r * L * C * S; }
+};
+
+struct Sketch {
+  float* dev = nullptr;
+  std::vector<long long> off;  // per site
+};
+
+std::vector<int> bond_caps(const std::vector<int>& chiX, const std::vector<int>& phys, int chi) {
+  const int L = (int)phys.size();
+  std::vector<int> r(L > 0 ? L - 1 : 0);
+  for (int i = 0; i < L - 1; ++i) r[i] = std::min(chi, chiX[i]);
+  int prev = 1;
+  for (int i = 0; i < L - 1; ++i) {
+    r[i] = std::min(r[i], prev * phys[i]);
+    prev = r[i];
+  }
+  int nxt = 1;
+  for (int i = L - 2; i >= 0; --i) {
+    r[i] = std::min(r[i], nxt * phys[i + 1]);
+    nxt = r[i];
+  }
+  return r;
+}
+
+}  // namespace
+
+struct pepsvmc_ctx {
+  pepsvmc_config cfg{};
+  cudaStream_t st = nullptr;
+  std::string err;
+  int C = 0, Ly = 0, Lx = 0, D = 0, chi = 0, nfit = 1, Lmax = 0;
+  long long P = 0, Ph = 0, S = 0, S4 = 0, SI = 0;
+  Orient O[4];
+  std::vector<long long> site_off, site_half_off;  // original sites
+  std::vector<int> site_size;
+  std::vector<long long> perm_site_off[4];
+  long long launches = 0;
+  unsigned long long sweep_counter = 0;
+  bool top_valid = false, have_grad = false, have_measure = false;
+  int trace_on = 0;
+  std::vector<double> sketch_host;
+  std::map<std::string, Sketch> sketches;
+  std::vector<int> trivial_bond;
+
+  // device memory
+  std::vector<void*> allocs;
+  double* master = nullptr;
+  double* grad = nullptr;
+  double* sumG = nullptr;
+  double* sumGE = nullptr;
+  double* sums = nullptr;
+  float* perm[4][2] = {};
+  int* perm_map[4][2] = {};
+  int8_t* spins = nullptr;
+  float* ones = nullptr;
+  double* zeros_d = nullptr;
+  Store st_top, st_bot, st_colbot, st_coltop;
+  float *envL = nullptr, *envR = nullptr, *envRf = nullptr;
+  float *l3[2] = {}, *fl = nullptr;
+  float *tmp1 = nullptr, *tmp2 = nullptr;
+  float *R4 = nullptr, *l4[2] = {}, *fl4 = nullptr, *ptop[2] = {}, *pbot[2] = {};
+  float* G = nullptr;
+  double *eloc = nullptr, *den = nullptr, *logpsi = nullptr;
+  int8_t* sign = nullptr;
+  int* exps = nullptr;
+  unsigned* status = nullptr;
+  unsigned long long* counters = nullptr;
+  double* trace_ratio = nullptr;
+  int8_t* trace_dec = nullptr;
+  int* elem_site = nullptr;
+  long long *d_site_half_off = nullptr, *d_site_full_off = nullptr;
+  int *d_site_size = nullptr, *d_site_spin = nullptr;
+
+  // ------------------------------------------------------------------ helpers
+  bool dry = false;                                      // no device: validate only
+  uintptr_t fake_next = (uintptr_t)1 << 44;
+  std::vector<std::pair<uintptr_t, size_t>> regions;     // every allocation (bounds checks)
+
+  template <typename T>
+  cudaError_t alloc(T** p, size_t n) {
+    void* q = nullptr;
+    const size_t bytes = n * sizeof(T);
+    if (dry) {
+      q = reinterpret_cast<void*>(fake_next);
+      fake_next += (bytes + 4096) & ~(size_t)255;
+    } else {
+      cudaError_t e = cudaMalloc(&q, bytes + 256);
+      if (e != cudaSuccess) return e;
+      allocs.push_back(q);
+    }
+    regions.push_back({reinterpret_cast<uintptr_t>(q), bytes});
+    *p = reinterpret_cast<T*>(q);
+    return cudaSuccess;
+  }
+
+  // True when elements [0, max_off] of p (element size esz) lie in one allocation.
+  bool span(const void* p, long long max_off, size_t esz, const char* what) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    if (!p || max_off < 0) {
+      err = std::string("bounds check failed (null or negative span): ") + what;
+      return false;
+    }
+    const uintptr_t end = a + (uintptr_t)(max_off + 1) * esz;
+    for (const auto& r : regions)
+      if (a >= r.first && a < r.first + r.second) {
+        if (end <= r.first + r.second) return true;
+        break;
+      }
+    char buf[256];
+    snprintf(buf, sizeof(buf), "bounds check failed: %s (max offset %lld)", what, max_off);
+    err = buf;
+    return false;
+  }
+
+  cudaError_t cp(void* dst, const void* src, size_t bytes, cudaMemcpyKind k) {
+    if (dry || bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, k, st);
+  }
+  cudaError_t ms(void* dst, int v, size_t bytes) { return dry ? cudaSuccess : cudaMemsetAsync(dst, v, bytes, st); }
+  cudaError_t sync() { return dry ? cudaSuccess : cudaStreamSynchronize(st); }
+  cudaError_t cps(void* dst, const void* src, size_t bytes, cudaMemcpyKind k) {
+    cudaError_t e = cp(dst, src, bytes, k);
+    return e == cudaSuccess ? sync() : e;
+  }
+
+  int nbonds() const { return 2 * Lx * Ly - Lx - Ly; }
+
+  void orig(int o, int kp, int mp, int& k, int& m) const {
+    const Orient& Ob = O[o];
+    const int kk = Ob.vf ? (Ob.Ly - 1 - kp) : kp;
+    if (!Ob.tr) { k = kk; m = mp; } else { k = mp; m = kk; }
+  }
+
+  SiteOp site(int o, int kp, int mp) const {
+    const Orient& Ob = O[o];
+    SiteOp s;
+    s.Dl = mp == 0 ? 1 : D;
+    s.Dr = mp == Ob.Lx - 1 ? 1 : D;
+    s.Du = kp == 0 ? 1 : D;
+    s.Dd = kp == Ob.Ly - 1 ? 1 : D;
+    s.size = (long long)s.Dl * s.Dr * s.Du * s.Dd;
+    const long long off = perm_site_off[o][(size_t)kp * Ob.Lx + mp];
+    s.lurd = perm[o][0] + off;
+    s.urld = perm[o][1] + off;
+    int k, m;
+    orig(o, kp, mp, k, m);
+    s.spin = k * Lx + m;
+    return s;
+  }
+
+  View trivial_view() const { return View{ones, 0, 1, &trivial_bond, zeros_d}; }
+
+  View view(const Store& s, int row, int slot) const {
+    if (row == 0) return trivial_view();
+    return View{s.row_ptr(slot, C, S), (long long)C * S, S, &s.bond[row], s.logs + (size_t)slot * C};
+  }
+
+  static long long scatter_max(int M, int c2, int c3, long long s1, long long s2, long long s3) {
+    const int c23 = c2 * c3;
+    return (long long)((M - 1) / c23) * s1 + (long long)(c2 - 1) * s2 + (long long)(c3 - 1) * s3;
+  }
+
+  cudaError_t gemm(GemmDesc& g) {
+    g.batch = C;
+    if (g.M % (g.cm2 * g.cm3) || g.N % (g.cn2 * g.cn3)) {
+      err = "contraction layout: scattered extents do not divide M or N";
+      return cudaErrorInvalidValue;
+    }
+    const long long b1 = C - 1;
+    if (!span(g.A, b1 * g.bsA + (long long)(g.M - 1) * g.sAm + (long long)(g.K - 1) * g.sAk, 4, "gemm A") ||
+        !span(g.B, (g.sel ? g.ssB : 0) + b1 * g.bsB + (long long)(g.K - 1) * g.sBk + (long long)(g.N - 1) * g.sBn, 4,
+              "gemm B") ||
+        !span(g.C, b1 * g.bsC + scatter_max(g.M, g.cm2, g.cm3, g.sCm1, g.sCm2, g.sCm3) +
+                       scatter_max(g.N, g.cn2, g.cn3, g.sCn1, g.sCn2, g.sCn3), 4, "gemm C") ||
+        (g.sel && !span(g.sel, b1 * g.sel_stride, 1, "gemm spin selector")) ||
+        (g.inv_scale && !span(g.inv_scale, b1, 8, "gemm scale")))
+      return cudaErrorInvalidValue;
+    ++launches;
+    return gemm_f32(g, gemm_f32_pick(g), st);
+  }
+
+  cudaError_t qr(const float* Y, long long bsY, long long yrs, long long ycs, float* Q, long long bsQ, long long qrs,
+                 long long qcs, int rows, int cols, int batch) {
+    const long long b1 = batch - 1;
+    if (!span(Y, b1 * bsY + (long long)(rows - 1) * yrs + (long long)(cols - 1) * ycs, 4, "qr input") ||
+        !span(Q, b1 * bsQ + (long long)(rows - 1) * qrs + (long long)(cols - 1) * qcs, 4, "qr output"))
+      return cudaErrorInvalidValue;
+    if (rows < cols) {
+      err = "qr: fewer rows than columns";
+      return cudaErrorInvalidValue;
+    }
+    ++launches;
+    return qr_pos_batched(Y, bsY, yrs, ycs, Q, bsQ, qrs, qcs, rows, cols, batch, st);
+  }
+
+  // Per-chain array span: chains 0..C-1 with stride bs, n entries each.
+  bool chains(const void* p, long long bs, long long n, size_t esz, const char* what) {
+    return span(p, (long long)(C - 1) * bs + n - 1, esz, what);
+  }
+
+  cudaError_t dot(const float* a, long long bsa, const float* b, long long bsb, int n, double* out) {
+    if (!chains(a, bsa, n, 4, "dot a") || !chains(b, bsb, n, 4, "dot b") || !chains(out, 1, 1, 8, "dot out"))
+      return cudaErrorInvalidValue;
+    ++launches;
+    return k_dot(a, bsa, b, bsb, n, out, C, status, st);
+  }
+
+  cudaError_t ratio(const float* a, long long bsa, const float* b, long long bsb, int n, int si, int sj,
+                    double halfJ) {
+    if (!chains(a, bsa, n, 4, "ratio a") || !chains(b, bsb, n, 4, "ratio b") ||
+        !chains(spins, (long long)Ly * Lx, (long long)std::max(si, sj) + 1, 1, "ratio spins"))
+      return cudaErrorInvalidValue;
+    ++launches;
+    return k_ratio_accum(a, bsa, b, bsb, n, den, spins, (long long)Ly * Lx, si, sj, halfJ, eloc, C, status, st);
+  }
+
+  cudaError_t logpsi_of(const float* x, long long bs, const double* logT, const double* logB) {
+    if (!chains(x, bs, 1, 4, "logpsi x") || !chains(logT, 1, 1, 8, "logT") || !chains(logB, 1, 1, 8, "logB"))
+      return cudaErrorInvalidValue;
+    ++launches;
+    return k_logpsi(x, bs, exps, logT, logB, logpsi, sign, C, status, st);
+  }
+
+  void sel(GemmDesc& g, const SiteOp& a, const float* base, int flip) const {
+    g.B = base;
+    g.ssB = a.size;
+    g.bsB = 0;
+    g.sel = spins + a.spin;
+    g.sel_stride = (long long)Ly * Lx;
+    g.sel_xor = flip;
+  }
+
+  // --------------------------------------------------------- contractions
+  // Three-line left step (App. C, Fig. "contraction" (c)): E (cT,Dl,cB) -> out (cT2,Dr,cB2).
+  cudaError_t left3(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
+                    const SiteOp& a, int flip, const float* B, long long bsB, int cB2, float* out,
+                    long long bsO) {
+    const int Dl = a.Dl, Dr = a.Dr, Du = a.Du, Dd = a.Dd;
+    GemmDesc g;
+    g.M = Dl * cB; g.N = Du * cT2; g.K = cT;
+    g.A = E; g.sAm = 1; g.sAk = (long long)Dl * cB; g.bsA = bsE;
+    g.B = T; g.sBk = (long long)Du * cT2; g.sBn = 1; g.bsB = bsT;
+    g.C = tmp1; g.bsC = SI;
+    g.cm2 = cB; g.sCm1 = Du; g.sCm2 = (long long)cT2 * Dl * Du;
+    g.cn2 = cT2; g.sCn1 = 1; g.sCn2 = (long long)Dl * Du;
+    PV_CUDA(gemm(g));
+    GemmDesc h;
+    h.M = cB * cT2; h.N = Dr * Dd; h.K = Dl * Du;
+    h.A = tmp1; h.sAm = (long long)Dl * Du; h.sAk = 1; h.bsA = SI;
+    sel(h, a, a.lurd, flip); h.sBk = (long long)Dr * Dd; h.sBn = 1;
+    h.C = tmp2; h.bsC = SI;
+    h.cm2 = cT2; h.sCm1 = Dd; h.sCm2 = (long long)Dr * cB * Dd;
+    h.cn2 = Dd; h.sCn1 = (long long)cB * Dd; h.sCn2 = 1;
+    PV_CUDA(gemm(h));
+    GemmDesc q;
+    q.M = cT2 * Dr; q.N = cB2; q.K = cB * Dd;
+    q.A = tmp2; q.sAm = (long long)cB * Dd; q.sAk = 1; q.bsA = SI;
+    q.B = B; q.sBk = cB2; q.sBn = 1; q.bsB = bsB;
+    q.C = out; q.bsC = bsO; q.sCm1 = cB2; q.sCn1 = 1;
+    return gemm(q);
+  }
+
+  // Three-line right step: E (cT2,Dr,cB2) -> out (cT,Dl,cB).
+  cudaError_t right3(const float* E, long long bsE, int cT2, int cB2, const float* T, long long bsT, int cT,
+                     const SiteOp& a, int flip, const float* B, long long bsB, int cB, float* out,
+                     long long bsO) {
+    const int Dl = a.Dl, Dr = a.Dr, Du = a.Du, Dd = a.Dd;
+    GemmDesc g;
+    g.M = cT * Du; g.N = Dr * cB2; g.K = cT2;
+    g.A = T; g.sAm = cT2; g.sAk = 1; g.bsA = bsT;
+    g.B = E; g.sBk = (long long)Dr * cB2; g.sBn = 1; g.bsB = bsE;
+    g.C = tmp1; g.bsC = SI;
+    g.cm2 = Du; g.sCm1 = (long long)cB2 * Du * Dr; g.sCm2 = Dr;
+    g.cn2 = cB2; g.sCn1 = 1; g.sCn2 = (long long)Du * Dr;
+    PV_CUDA(gemm(g));
+    GemmDesc h;
+    h.M = cT * cB2; h.N = Dl * Dd; h.K = Du * Dr;
+    h.A = tmp1; h.sAm = (long long)Du * Dr; h.sAk = 1; h.bsA = SI;
+    sel(h, a, a.urld, flip); h.sBk = (long long)Dl * Dd; h.sBn = 1;
+    h.C = tmp2; h.bsC = SI;
+    h.cm2 = cB2; h.sCm1 = (long long)Dl * Dd * cB2; h.sCm2 = 1;
+    h.cn2 = Dd; h.sCn1 = (long long)Dd * cB2; h.sCn2 = cB2;
+    PV_CUDA(gemm(h));
+    GemmDesc q;
+    q.M = cT * Dl; q.N = cB; q.K = Dd * cB2;
+    q.A = tmp2; q.sAm = (long long)Dd * cB2; q.sAk = 1; q.bsA = SI;
+    q.B = B; q.sBk = 1; q.sBn = (long long)Dd * cB2; q.bsB = bsB;
+    q.C = out; q.bsC = bsO; q.sCm1 = cB; q.sCn1 = 1;
+    return gemm(q);
+  }
+
+  // Optimal site of the fit (App. B): Y (cV,Dd,cV2) = L (cT,Dl,cV) . T . a . R (cT2,Dr,cV2).
+  cudaError_t proj3(const float* Lf, long long bsL, int cT, int cV, const float* T, long long bsT, int cT2,
+                    const SiteOp& a, const float* Rf, long long bsR, int cV2, float* Y, long long bsY) {
+    const int Dl = a.Dl, Dr = a.Dr, Du = a.Du, Dd = a.Dd;
+    GemmDesc g;
+    g.M = Dl * cV; g.N = Du * cT2; g.K = cT;
+    g.A = Lf; g.sAm = 1; g.sAk = (long long)Dl * cV; g.bsA = bsL;
+    g.B = T; g.sBk = (long long)Du * cT2; g.sBn = 1; g.bsB = bsT;
+    g.C = tmp1; g.bsC = SI;
+    g.cm2 = cV; g.sCm1 = Du; g.sCm2 = (long long)cT2 * Dl * Du;
+    g.cn2 = cT2; g.sCn1 = 1; g.sCn2 = (long long)Dl * Du;
+    PV_CUDA(gemm(g));
+    GemmDesc h;
+    h.M = cV * cT2; h.N = Dr * Dd; h.K = Dl * Du;
+    h.A = tmp1; h.sAm = (long long)Dl * Du; h.sAk = 1; h.bsA = SI;
+    sel(h, a, a.lurd, 0); h.sBk = (long long)Dr * Dd; h.sBn = 1;
+    h.C = tmp2; h.bsC = SI;
+    h.cm2 = cT2; h.sCm1 = (long long)Dd * cT2 * Dr; h.sCm2 = Dr;
+    h.cn2 = Dd; h.sCn1 = 1; h.sCn2 = (long long)cT2 * Dr;
+    PV_CUDA(gemm(h));
+    GemmDesc q;
+    q.M = cV * Dd; q.N = cV2; q.K = cT2 * Dr;
+    q.A = tmp2; q.sAm = (long long)cT2 * Dr; q.sAk = 1; q.bsA = SI;
+    q.B = Rf; q.sBk = cV2; q.sBn = 1; q.bsB = bsR;
+    q.C = Y; q.bsC = bsY; q.sCm1 = cV2; q.sCn1 = 1;
+    return gemm(q);
+  }
+
+  // Defect network (Eq. (7)) divided by Psi: G[l][r][u][d] = L.T.B.R / den.
+  cudaError_t delta3(const float* Lf, long long bsL, int cT, int cB, const float* T, long long bsT, int cT2,
+                     const SiteOp& a, const float* B, long long bsB, int cB2, const float* Rf, long long bsR,
+                     const double* dn, float* Gout, long long bsG) {
+    const int Dl = a.Dl, Dr = a.Dr, Du = a.Du, Dd = a.Dd;
+    GemmDesc g;
+    g.M = Dl * cB; g.N = Du * cT2; g.K = cT;
+    g.A = Lf; g.sAm = 1; g.sAk = (long long)Dl * cB; g.bsA = bsL;
+    g.B = T; g.sBk = (long long)Du * cT2; g.sBn = 1; g.bsB = bsT;
+    g.C = tmp1; g.bsC = SI;
+    g.cm2 = cB; g.sCm1 = (long long)Du * cB * cT2; g.sCm2 = cT2;
+    g.cn2 = cT2; g.sCn1 = (long long)cB * cT2; g.sCn2 = 1;
+    PV_CUDA(gemm(g));
+    GemmDesc p;
+    p.M = cB * Dd; p.N = cT2 * Dr; p.K = cB2;
+    p.A = B; p.sAm = cB2; p.sAk = 1; p.bsA = bsB;
+    p.B = Rf; p.sBk = 1; p.sBn = cB2; p.bsB = bsR;
+    p.C = tmp2; p.bsC = SI;
+    p.cm2 = Dd; p.sCm1 = (long long)cT2 * Dd * Dr; p.sCm2 = Dr;
+    p.cn2 = Dr; p.sCn1 = (long long)Dd * Dr; p.sCn2 = 1;
+    PV_CUDA(gemm(p));
+    GemmDesc q;
+    q.M = Dl * Du; q.N = Dd * Dr; q.K = cB * cT2;
+    q.A = tmp1; q.sAm = (long long)cB * cT2; q.sAk = 1; q.bsA = SI;
+    q.B = tmp2; q.sBk = (long long)Dd * Dr; q.sBn = 1; q.bsB = SI;
+    q.C = Gout; q.bsC = bsG;
+    q.cm2 = Du; q.sCm1 = (long long)Dr * Du * Dd; q.sCm2 = Dd;
+    q.cn2 = Dr; q.sCn1 = 1; q.sCn2 = (long long)Du * Dd;
+    q.inv_scale = dn;
+    return gemm(q);
+  }
+
+  // Four-line left step of rows (k, k+1): E (cT,D1l,D2l,cB) -> out (cT2,D1r,D2r,cB2).
+  cudaError_t left4(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
+                    const SiteOp& a1, int f1, const SiteOp& a2, int f2, const float* B, long long bsB, int cB2,
+                    float* out, long long bsO) {
+    const int D1l = a1.Dl, D1r = a1.Dr, Du1 = a1.Du, Dd1 = a1.Dd;
+    const int D2l = a2.Dl, D2r = a2.Dr, Dd2 = a2.Dd;
+    GemmDesc g;
+    g.M = D1l * D2l * cB; g.N = Du1 * cT2; g.K = cT;
+    g.A = E; g.sAm = 1; g.sAk = (long long)D1l * D2l * cB; g.bsA = bsE;
+    g.B = T; g.sBk = (long long)Du1 * cT2; g.sBn = 1; g.bsB = bsT;
+    g.C = tmp1; g.bsC = SI;
+    g.cm2 = D2l * cB; g.sCm1 = Du1; g.sCm2 = (long long)cT2 * D1l * Du1;
+    g.cn2 = cT2; g.sCn1 = 1; g.sCn2 = (long long)D1l * Du1;
+    PV_CUDA(gemm(g));
+    GemmDesc h;
+    h.M = D2l * cB * cT2; h.N = D1r * Dd1; h.K = D1l * Du1;
+    h.A = tmp1; h.sAm = (long long)D1l * Du1; h.sAk = 1; h.bsA = SI;
+    sel(h, a1, a1.lurd, f1); h.sBk = (long long)D1r * Dd1; h.sBn = 1;
+    h.C = tmp2; h.bsC = SI;
+    h.cm2 = cB * cT2; h.sCm1 = Dd1; h.sCm2 = (long long)D1r * D2l * Dd1;
+    h.cn2 = Dd1; h.sCn1 = (long long)D2l * Dd1; h.sCn2 = 1;
+    PV_CUDA(gemm(h));
+    GemmDesc q;
+    q.M = cB * cT2 * D1r; q.N = D2r * Dd2; q.K = D2l * Dd1;
+    q.A = tmp2; q.sAm = (long long)D2l * Dd1; q.sAk = 1; q.bsA = SI;
+    sel(q, a2, a2.lurd, f2); q.sBk = (long long)D2r * Dd2; q.sBn = 1;
+    q.C = tmp1; q.bsC = SI;
+    q.cm2 = cT2 * D1r; q.sCm1 = Dd2; q.sCm2 = (long long)D2r * cB * Dd2;
+    q.cn2 = Dd2; q.sCn1 = (long long)cB * Dd2; q.sCn2 = 1;
+    PV_CUDA(gemm(q));
+    GemmDesc w;
+    w.M = cT2 * D1r * D2r; w.N = cB2; w.K = cB * Dd2;
+    w.A = tmp1; w.sAm = (long long)cB * Dd2; w.sAk = 1; w.bsA = SI;
+    w.B = B; w.sBk = cB2; w.sBn = 1; w.bsB = bsB;
+    w.C = out; w.bsC = bsO; w.sCm1 = cB2; w.sCn1 = 1;
+    return gemm(w);
+  }
+
+  // Four-line right step: E (cT2,D1r,D2r,cB2) -> out (cT,D1l,D2l,cB).
+  cudaError_t right4(const float* E, long long bsE, int cT2, int cB2, const float* T, long long bsT, int cT,
+                     const SiteOp& a1, int f1, const SiteOp& a2, int f2, const float* B, long long bsB, int cB,
+                     float* out, long long bsO) {
+    const int D1l = a1.Dl, D1r = a1.Dr, Du1 = a1.Du, Dd1 = a1.Dd;
+    const int D2l = a2.Dl, D2r = a2.Dr, Dd2 = a2.Dd;
+    GemmDesc g;
+    g.M = cT * Du1; g.N = D1r * D2r * cB2; g.K = cT2;
+    g.A = T; g.sAm = cT2; g.sAk = 1; g.bsA = bsT;
+    g.B = E; g.sBk = (long long)D1r * D2r * cB2; g.sBn = 1; g.bsB = bsE;
+    g.C = tmp1; g.bsC = SI;
+    g.cm2 = Du1; g.sCm1 = (long long)D2r * cB2 * Du1 * D1r; g.sCm2 = D1r;
+    g.cn2 = D2r * cB2; g.sCn1 = 1; g.sCn2 = (long long)Du1 * D1r;
+    PV_CUDA(gemm(g));
+    GemmDesc h;
+    h.M = cT * D2r * cB2; h.N = D1l * Dd1; h.K = Du1 * D1r;
+    h.A = tmp1; h.sAm = (long long)Du1 * D1r; h.sAk = 1; h.bsA = SI;
+    sel(h, a1, a1.urld, f1); h.sBk = (long long)D1l * Dd1; h.sBn = 1;
+    h.C = tmp2; h.bsC = SI;
+    h.cm2 = D2r; h.cm3 = cB2;
+    h.sCm1 = (long long)D1l * cB2 * Dd1 * D2r; h.sCm2 = 1; h.sCm3 = (long long)Dd1 * D2r;
+    h.cn2 = Dd1; h.sCn1 = (long long)cB2 * Dd1 * D2r; h.sCn2 = D2r;
+    PV_CUDA(gemm(h));
+    GemmDesc q;
+    q.M = cT * D1l * cB2; q.N = D2l * Dd2; q.K = Dd1 * D2r;
+    q.A = tmp2; q.sAm = (long long)Dd1 * D2r; q.sAk = 1; q.bsA = SI;
+    sel(q, a2, a2.urld, f2); q.sBk = (long long)D2l * Dd2; q.sBn = 1;
+    q.C = tmp1; q.bsC = SI;
+    q.cm2 = cB2; q.sCm1 = (long long)D2l * Dd2 * cB2; q.sCm2 = 1;
+    q.cn2 = Dd2; q.sCn1 = (long long)Dd2 * cB2; q.sCn2 = cB2;
+    PV_CUDA(gemm(q));
+    GemmDesc w;
+    w.M = cT * D1l * D2l; w.N = cB; w.K = Dd2 * cB2;
+    w.A = tmp1; w.sAm = (long long)Dd2 * cB2; w.sAk = 1; w.bsA = SI;
+    w.B = B; w.sBk = 1; w.sBn = (long long)Dd2 * cB2; w.bsB = bsB;
+    w.C = out; w.bsC = bsO; w.sCm1 = cB; w.sCn1 = 1;
+    return gemm(w);
+  }
+
+  cudaError_t norm2(float* x, long long bs, int n, float* x2 = nullptr, int n2 = 0, float* x3 = nullptr,
+                    int n3 = 0, int* ex = nullptr) {
+    if (!chains(x, bs, n, 4, "normalize x") || (x2 && !chains(x2, bs, n2, 4, "normalize x2")) ||
+        (x3 && !chains(x3, bs, n3, 4, "normalize x3")))
+      return cudaErrorInvalidValue;
+    ++launches;
+    return k_normalize_pow2(x, bs, n, x2, bs, n2, x3, bs, n3, ex, C, status, st);
+  }
+
+  // ------------------------------------------------------ boundary MPS (App. B)
+  const Sketch& sketch_for(const std::vector<int>& vb, const std::vector<int>& p, cudaError_t& e) {
+    std::string key;
+    for (int v : vb) key += std::to_string(v) + ",";
+    key += "|";
+    for (int v : p) key += std::to_string(v) + ",";
+    auto it = sketches.find(key);
+    e = cudaSuccess;
+    if (it != sketches.end()) return it->second;
+    Sketch sk;
+    const int L = (int)p.size();
+    std::vector<float> host;
+    for (int m = 0; m < L; ++m) {
+      sk.off.push_back((long long)host.size());
+      for (int a = 0; a < vb[m]; ++a)
+        for (int d = 0; d < p[m]; ++d)
+          for (int b = 0; b < vb[m + 1]; ++b)
+            host.push_back((float)sketch_host[(((size_t)m * chi + a) * D + d) * chi + b]);
+    }
+    if ((e = alloc(&sk.dev, host.size())) != cudaSuccess) return sketches[key];
+    if ((e = cp(sk.dev, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return sketches[key];
+    // right-orthonormal rows for sites m >= 1: QR of the transposed site, Q^T written back
+    for (int m = 1; m < L; ++m) {
+      const int rows = p[m] * vb[m + 1], cols = vb[m];
+      float* s = sk.dev + sk.off[m];
+      if ((e = qr(s, 0, 1, rows, s, 0, 1, rows, rows, cols, 1)) != cudaSuccess) return sketches[key];
+    }
+    e = sync();
+    return sketches[key] = sk;
+  }
+
+  // V = fit(M_k |Tin>) into store row `slot`, bonds recorded as store.bond[row].
+  cudaError_t compress(int o, int k, const View& Tin, Store& out, int row, int slot) {
+    const Orient& Ob = O[o];
+    const int L = Ob.Lx;
+    const std::vector<int>& tb = *Tin.bond;
+    std::vector<int> p(L), chiX(L > 1 ? L - 1 : 0);
+    std::vector<SiteOp> a(L);
+    for (int m = 0; m < L; ++m) {
+      a[m] = site(o, k, m);
+      p[m] = a[m].Dd;
+      if (m < L - 1) chiX[m] = tb[m + 1] * a[m].Dr;
+    }
+    const std::vector<int> r = bond_caps(chiX, p, chi);
+    std::vector<int> vb(L + 1, 1);
+    for (int m = 0; m < L - 1; ++m) vb[m + 1] = r[m];
+    out.bond[row] = vb;
+    cudaError_t e;
+    const Sketch& W = sketch_for(vb, p, e);
+    PV_CUDA(e);
+    float* Vb = out.row_ptr(slot, C, S);
+    const long long vss = (long long)C * S;
+    double* log_out = out.logs + (size_t)slot * C;
+    auto envLp = [&](int m) { return envL + (long long)m * C * S; };
+    auto envRp = [&](int m) { return envR + (long long)m * C * S; };
+    // right environments of the starting guess
+    for (int m = L - 1; m >= 1; --m) {
+      const bool edge = (m == L - 1);
+      PV_CUDA(right3(edge ? ones : envRp(m + 1), edge ? 1 : S, tb[m + 1], vb[m + 1], Tin.site(m),
+                     Tin.chain_stride, tb[m], a[m], 0, W.dev + W.off[m], 0, vb[m], envRp(m), S));
+      PV_CUDA(norm2(envRp(m), S, tb[m] * a[m].Dl * vb[m]));
+    }
+    for (int sw = 0; sw < nfit; ++sw) {
+      if (sw % 2 == 0) {
+        PV_CUDA(ms(exps, 0, C * sizeof(int)));
+        for (int m = 0; m < L; ++m) {
+          const float* Lin = m == 0 ? ones : envLp(m);
+          const long long bsL = m == 0 ? 1 : S;
+          const float* Rin = m == L - 1 ? ones : envRp(m + 1);
+          const long long bsR = m == L - 1 ? 1 : S;
+          float* Vs = Vb + m * vss;
+          PV_CUDA(proj3(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], Rin, bsR,
+                        vb[m + 1], Vs, S));
+          if (m < L - 1) {
+            PV_CUDA(qr(Vs, S, vb[m + 1], 1, Vs, S, vb[m + 1], 1, vb[m] * p[m], vb[m + 1], C));
+            PV_CUDA(left3(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], 0, Vs, S,
+                          vb[m + 1], envLp(m + 1), S));
+            PV_CUDA(norm2(envLp(m + 1), S, tb[m + 1] * a[m].Dr * vb[m + 1], nullptr, 0, nullptr, 0, exps));
+          }
+        }
+      } else {
+        for (int m = L - 1; m >= 0; --m) {
+          const float* Lin = m == 0 ? ones : envLp(m);
+          const long long bsL = m == 0 ? 1 : S;
+          const float* Rin = m == L - 1 ? ones : envRp(m + 1);
+          const long long bsR = m == L - 1 ? 1 : S;
+          float* Vs = Vb + m * vss;
+          PV_CUDA(proj3(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], Rin, bsR,
+                        vb[m + 1], Vs, S));
+          if (m > 0) {
+            const int rows = p[m] * vb[m + 1];
+            PV_CUDA(qr(Vs, S, 1, rows, Vs, S, 1, rows, rows, vb[m], C));
+            PV_CUDA(right3(Rin, bsR, tb[m + 1], vb[m + 1], Tin.site(m), Tin.chain_stride, tb[m], a[m], 0, Vs, S,
+                           vb[m], envRp(m), S));
+            PV_CUDA(norm2(envRp(m), S, tb[m] * a[m].Dl * vb[m]));
+          }
+        }
+      }
+    }
+    float* center = Vb + (long long)(L - 1) * vss;
+    if (!chains(center, S, vb[L - 1] * p[L - 1], 4, "mps centre") || !chains(log_out, 1, 1, 8, "mps log") ||
+        !chains(Tin.logs, 1, 1, 8, "mps log in"))
+      return cudaErrorInvalidValue;
+    ++launches;
+    return k_mps_normalize(center, S, vb[L - 1] * p[L - 1], exps, Tin.logs, log_out, C, status, st);
+  }
+
+  // All top environments of orientation o (rows 1..Ly_o-1 into store, one slot per row).
+  cudaError_t top_down_all(int o, Store& s) {
+    for (int k = 0; k + 1 < O[o].Ly; ++k) PV_CUDA(compress(o, k, view(s, k, k), s, k + 1, k + 1));
+    return cudaSuccess;
+  }
+
+  // --------------------------------------------- sequential sweep (Sec. II A, Eq. (9))
+  // Horizontal bonds of every row of orientation o.  `top` receives T_k (slot = row, or
+  // row % 2 when `pingpong`), `bot` must hold the top environments of the upside-down
+  // orientation for the configuration at the start of the phase.
+  cudaError_t row_phase(int o, Store& top, bool pingpong, Store& bot, int bond_base) {
+    const Orient& Ob = O[o];
+    const int Lyo = Ob.Ly, Lxo = Ob.Lx;
+    auto slot_of = [&](int row) { return pingpong ? (row % 2) : row; };
+    auto envRp = [&](int m) { return envR + (long long)m * C * S; };
+    auto envRfp = [&](int m) { return envRf + (long long)m * C * S; };
+    for (int k = 0; k < Lyo; ++k) {
+      const View T = view(top, k, slot_of(k));
+      const int kb = Lyo - 1 - k;
+      const View B = view(bot, kb, kb);
+      const std::vector<int>& tb = *T.bond;
+      const std::vector<int>& bb = *B.bond;
+      std::vector<SiteOp> a(Lxo);
+      for (int m = 0; m < Lxo; ++m) a[m] = site(o, k, m);
+      for (int m = Lxo - 1; m >= 1; --m) {
+        const bool edge = (m == Lxo - 1);
+        const float* Ein = edge ? ones : envRp(m + 1);
+        const long long bsE = edge ? 1 : S;
+        PV_CUDA(right3(Ein, bsE, tb[m + 1], bb[m + 1], T.site(m), T.chain_stride, tb[m], a[m], 0, B.site(m),
+                       B.chain_stride, bb[m], envRp(m), S));
+        PV_CUDA(right3(Ein, bsE, tb[m + 1], bb[m + 1], T.site(m), T.chain_stride, tb[m], a[m], 1, B.site(m),
+                       B.chain_stride, bb[m], envRfp(m), S));
+        const int n = tb[m] * a[m].Dl * bb[m];
+        PV_CUDA(norm2(envRp(m), S, n, envRfp(m), n));
+      }
+      const float* Lin = ones;
+      long long bsL = 1;
+      for (int m = 0; m + 1 < Lxo; ++m) {
+        PV_CUDA(left3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], 0, B.site(m),
+                      B.chain_stride, bb[m + 1], l3[1], S));
+        PV_CUDA(left3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], 1, B.site(m),
+                      B.chain_stride, bb[m + 1], fl, S));
+        MetropolisArgs ma{};
+        ma.cur = l3[1]; ma.bs_cur = S;
+        ma.Rcur = envRp(m + 1); ma.bs_Rcur = S;
+        ma.flip = fl; ma.bs_flip = S;
+        ma.Rflip = envRfp(m + 1); ma.bs_Rflip = S;
+        ma.n = tb[m + 1] * a[m].Dr * bb[m + 1];
+        ma.spins = spins; ma.spin_stride = (long long)Ly * Lx;
+        ma.site_a = a[m].spin; ma.site_b = a[m + 1].spin;
+        ma.key = cfg.seed; ma.sweep = sweep_counter;
+        ma.bond = bond_base + k * (Lxo - 1) + m;
+        ma.out = l3[0]; ma.bs_out = S;
+        ma.trace_ratio = trace_on ? trace_ratio : nullptr;
+        ma.trace_dec = trace_on ? trace_dec : nullptr;
+        ma.trace_stride = nbonds();
+        ma.counters = counters; ma.status = status;
+        if (!chains(ma.cur, S, ma.n, 4, "metropolis cur") || !chains(ma.Rcur, S, ma.n, 4, "metropolis R") ||
+            !chains(ma.flip, S, ma.n, 4, "metropolis flip") || !chains(ma.Rflip, S, ma.n, 4, "metropolis Rf") ||
+            !chains(ma.out, S, ma.n, 4, "metropolis out") ||
+            !chains(spins, ma.spin_stride, std::max(ma.site_a, ma.site_b) + 1, 1, "metropolis spins") ||
+            (ma.trace_ratio && !chains(ma.trace_ratio, nbonds(), ma.bond + 1, 8, "trace")))
+          return cudaErrorInvalidValue;
+        ++launches;
+        PV_CUDA(k_metropolis(ma, C, st));
+        Lin = l3[0];
+        bsL = S;
+      }
+      if (k + 1 < Lyo) PV_CUDA(compress(o, k, T, top, k + 1, slot_of(k + 1)));
+    }
+    return cudaSuccess;
+  }
+
+  cudaError_t sweep_once() {
+    // vertical bonds: columns of the transposed lattice (O2), bottom environments from O3
+    PV_CUDA(top_down_all(3, st_colbot));
+    PV_CUDA(row_phase(2, st_coltop, true, st_colbot, 0));
+    // horizontal bonds: rows (O0), bottom environments from O1
+    PV_CUDA(top_down_all(1, st_bot));
+    PV_CUDA(row_phase(0, st_top, false, st_bot, Lx * (Ly - 1)));
+    top_valid = true;
+    ++sweep_counter;
+    return cudaSuccess;
+  }
+
+  // ------------------------------------------------ measurement (Eqs. (3)-(7), App. C)
+  cudaError_t measure_dev() {
+    if (!top_valid) {
+      PV_CUDA(top_down_all(0, st_top));
+      top_valid = true;
+    }
+    PV_CUDA(top_down_all(1, st_bot));
+    ++launches;
+    PV_CUDA(k_eloc_diag(spins, Ly, Lx, cfg.J1, cfg.J2, eloc, C, st));
+    auto envRp = [&](int m) { return envR + (long long)m * C * S; };
+    auto envRfp = [&](int m) { return envRf + (long long)m * C * S; };
+    const int kstar = Ly / 2;
+    for (int k = 0; k < Ly; ++k) {
+      const View T = view(st_top, k, k);
+      const View B = view(st_bot, Ly - 1 - k, Ly - 1 - k);
+      const std::vector<int>& tb = *T.bond;
+      const std::vector<int>& bb = *B.bond;
+      std::vector<SiteOp> a(Lx);
+      for (int m = 0; m < Lx; ++m) a[m] = site(0, k, m);
+      for (int m = Lx - 1; m >= 1; --m) {
+        const bool edge = (m == Lx - 1);
+        const float* Ein = edge ? ones : envRp(m + 1);
+        const long long bsE = edge ? 1 : S;
+        PV_CUDA(right3(Ein, bsE, tb[m + 1], bb[m + 1], T.site(m), T.chain_stride, tb[m], a[m], 0, B.site(m),
+                       B.chain_stride, bb[m], envRp(m), S));
+        PV_CUDA(right3(Ein, bsE, tb[m + 1], bb[m + 1], T.site(m), T.chain_stride, tb[m], a[m], 1, B.site(m),
+                       B.chain_stride, bb[m], envRfp(m), S));
+        const int n = tb[m] * a[m].Dl * bb[m];
+        PV_CUDA(norm2(envRp(m), S, n, envRfp(m), n));
+      }
+      if (k == kstar) PV_CUDA(ms(exps, 0, C * sizeof(int)));
+      const float* Lin = ones;
+      long long bsL = 1;
+      for (int m = 0; m < Lx; ++m) {
+        const bool edge = (m == Lx - 1);
+        const float* Rin = edge ? ones : envRp(m + 1);
+        const long long bsR = edge ? 1 : S;
+        float* cur = l3[(m + 1) % 2];
+        const int n = tb[m + 1] * a[m].Dr * bb[m + 1];
+        PV_CUDA(left3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], 0, B.site(m),
+                      B.chain_stride, bb[m + 1], cur, S));
+        PV_CUDA(dot(cur, S, Rin, bsR, n, den));
+        if (!edge) {
+          PV_CUDA(left3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], 1, B.site(m),
+                        B.chain_stride, bb[m + 1], fl, S));
+          PV_CUDA(ratio(fl, S, envRfp(m + 1), S, n, a[m].spin, a[m + 1].spin, 0.5 * cfg.J1));
+        }
+        PV_CUDA(delta3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], B.site(m),
+                       B.chain_stride, bb[m + 1], Rin, bsR, den, G + site_half_off[(size_t)k * Lx + m], Ph));
+        if (!edge) {
+          PV_CUDA(norm2(cur, S, n, nullptr, 0, nullptr, 0, k == kstar ? exps : nullptr));
+        } else if (k == kstar) {
+          PV_CUDA(logpsi_of(cur, S, T.logs, B.logs));
+        }
+        Lin = cur;
+        bsL = S;
+      }
+    }
+    for (int k = 0; k + 1 < Ly; ++k) PV_CUDA(pair_terms(k));
+    have_measure = true;
+    return cudaSuccess;
+  }
+
+  // Vertical NN terms and both NNN diagonals of rows (k, k+1) by four-line environments.
+  cudaError_t pair_terms(int k) {
+    const View T = view(st_top, k, k);
+    const View B = view(st_bot, Ly - 2 - k, Ly - 2 - k);
+    const std::vector<int>& tb = *T.bond;
+    const std::vector<int>& bb = *B.bond;
+    std::vector<SiteOp> a1(Lx), a2(Lx);
+    for (int m = 0; m < Lx; ++m) {
+      a1[m] = site(0, k, m);
+      a2[m] = site(0, k + 1, m);
+    }
+    auto R4p = [&](int m) { return R4 + (long long)m * C * S4; };
+    for (int m = Lx - 1; m >= 1; --m) {
+      const bool edge = (m == Lx - 1);
+      PV_CUDA(right4(edge ? ones : R4p(m + 1), edge ? 1 : S4, tb[m + 1], bb[m + 1], T.site(m), T.chain_stride,
+                     tb[m], a1[m], 0, a2[m], 0, B.site(m), B.chain_stride, bb[m], R4p(m), S4));
+      PV_CUDA(norm2(R4p(m), S4, tb[m] * a1[m].Dl * a2[m].Dl * bb[m]));
+    }
+    const float* Lin = ones;
+    long long bsL = 1;
+    const float *Pt = nullptr, *Pb = nullptr;
+    for (int m = 0; m < Lx; ++m) {
+      const bool edge = (m == Lx - 1);
+      const float* Rin = edge ? ones : R4p(m + 1);
+      const long long bsR = edge ? 1 : S4;
+      const int n = tb[m + 1] * a1[m].Dr * a2[m].Dr * bb[m + 1];
+      float* cur = l4[(m + 1) % 2];
+      auto step = [&](const float* Ein, long long bsE, int f1, int f2, float* out) {
+        return left4(Ein, bsE, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a1[m], f1, a2[m], f2,
+                     B.site(m), B.chain_stride, bb[m + 1], out, S4);
+      };
+      PV_CUDA(step(Lin, bsL, 0, 0, cur));
+      PV_CUDA(dot(cur, S4, Rin, bsR, n, den));
+      PV_CUDA(step(Lin, bsL, 1, 1, fl4));
+      PV_CUDA(ratio(fl4, S4, Rin, bsR, n, a1[m].spin, a2[m].spin, 0.5 * cfg.J1));
+      float *Ptn = nullptr, *Pbn = nullptr;
+      if (cfg.J2 != 0.0) {
+        if (m >= 1) {
+          PV_CUDA(step(Pt, S4, 0, 1, fl4));
+          PV_CUDA(ratio(fl4, S4, Rin, bsR, n, a1[m - 1].spin, a2[m].spin, 0.5 * cfg.J2));
+          PV_CUDA(step(Pb, S4, 1, 0, fl4));
+          PV_CUDA(ratio(fl4, S4, Rin, bsR, n, a2[m - 1].spin, a1[m].spin, 0.5 * cfg.J2));
+        }
+        if (!edge) {
+          Ptn = ptop[(m + 1) % 2];
+          Pbn = pbot[(m + 1) % 2];
+          PV_CUDA(step(Lin, bsL, 1, 0, Ptn));
+          PV_CUDA(step(Lin, bsL, 0, 1, Pbn));
+        }
+      }
+      if (!edge) PV_CUDA(norm2(cur, S4, n, Ptn, Ptn ? n : 0, Pbn, Pbn ? n : 0));
+      Lin = cur;
+      bsL = S4;
+      Pt = Ptn;
+      Pb = Pbn;
+    }
+    return cudaSuccess;
+  }
+
+  // Psi of the current configuration contracted at row `row` (fresh environments).
+  cudaError_t amplitude_dev(int row) {
+    PV_CUDA(top_down_all(0, st_top));
+    top_valid = true;
+    PV_CUDA(top_down_all(1, st_bot));
+    const View T = view(st_top, row, row);
+    const View B = view(st_bot, Ly - 1 - row, Ly - 1 - row);
+    const std::vector<int>& tb = *T.bond;
+    const std::vector<int>& bb = *B.bond;
+    PV_CUDA(ms(exps, 0, C * sizeof(int)));
+    const float* Lin = ones;
+    long long bsL = 1;
+    for (int m = 0; m < Lx; ++m) {
+      const SiteOp a = site(0, row, m);
+      float* cur = l3[(m + 1) % 2];
+      PV_CUDA(left3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a, 0, B.site(m),
+                    B.chain_stride, bb[m + 1], cur, S));
+      if (m + 1 < Lx) {
+        PV_CUDA(norm2(cur, S, tb[m + 1] * a.Dr * bb[m + 1], nullptr, 0, nullptr, 0, exps));
+      } else {
+        PV_CUDA(logpsi_of(cur, S, T.logs, B.logs));
+      }
+      Lin = cur;
+      bsL = S;
+    }
+    return cudaSuccess;
+  }
+
+  cudaError_t refresh_perms() {
+    for (int o = 0; o < 4; ++o)
+      for (int t = 0; t < 2; ++t) {
+        ++launches;
+        PV_CUDA(k_gather_f32(perm[o][t], master, perm_map[o][t], P, st));
+      }
+    return cudaSuccess;
+  }
+
+  int check_status() {
+    unsigned h = 0;
+    cudaError_t e = cp(&h, status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = sync();
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (h) {
+      ms(status, 0, sizeof(unsigned));
+      if (h & ST_TIMEOUT) return fail(PEPSVMC_ETIMEOUT, "device wait budget exhausted");
+      if (h & ST_NONFINITE) return fail(PEPSVMC_ENONFINITE, "non-finite amplitude ratio or environment");
+      if (h & ST_ZEROPSI) return fail(PEPSVMC_EZEROPSI, "a configuration with Psi(S) = 0 was met");
+    }
+    return PEPSVMC_OK;
+  }
+
+  int fail(int code, const std::string& m) {
+    err = m;
+    return code;
+  }
+  int fail_cuda(cudaError_t e) {
+    if (e == cudaErrorInvalidValue && err.rfind("bounds check", 0) == 0) return PEPSVMC_EINVAL;
+    if (e == cudaErrorInvalidValue && err.rfind("contraction layout", 0) == 0) return PEPSVMC_EINVAL;
+    err = std::string("CUDA error: ") + cudaGetErrorString(e);
+    return PEPSVMC_ECUDA;
+  }
+};
+
+// ============================================================================= C ABI
+namespace {
+
+int validate(const pepsvmc_config* c, std::string& why) {
+  if (!c) { why = "null config"; return PEPSVMC_EINVAL; }
+  if (c->Ly < 1 || c->Lx < 1 || c->Ly > 64 || c->Lx > 64) { why = "Ly, Lx must be in 1..64"; return PEPSVMC_EINVAL; }
+  if ((c->Ly * c->Lx) % 2) { why = "Ly*Lx must be even (S^z = 0 sector)"; return PEPSVMC_EINVAL; }
+  if (c->D < 1 || c->D > 16) { why = "D must be in 1..16"; return PEPSVMC_EINVAL; }
+  if (c->chi < 1 || c->chi > 64) { why = "chi must be in 1..64"; return PEPSVMC_EINVAL; }
+  if ((long long)c->chi * c->chi * c->D * 2 * 4 > 200 * 1024) { why = "chi*chi*D too large for the QR kernel"; return PEPSVMC_EINVAL; }
+  if (c->n_chains < 1 || c->n_chains > (1 << 20)) { why = "n_chains must be >= 1"; return PEPSVMC_EINVAL; }
+  if (c->n_fit < 1 || c->n_fit % 2 == 0) { why = "n_fit must be odd and >= 1"; return PEPSVMC_EINVAL; }
+  if (c->precision != PEPSVMC_FP32 && c->precision != PEPSVMC_MIXED_BF16) { why = "unknown precision"; return PEPSVMC_EINVAL; }
+  if (c->precision == PEPSVMC_MIXED_BF16) { why = "precision MIXED_BF16 is not built in this library"; return PEPSVMC_EINVAL; }
+  for (int i = 0; i < 7; ++i)
+    if (c->reserved[i]) { why = "reserved fields must be zero"; return PEPSVMC_EINVAL; }
+  return PEPSVMC_OK;
+}
+
+int setup(pepsvmc_ctx* x, const double* tensors, const double* sketch) {
+  const int Ly = x->Ly, Lx = x->Lx, D = x->D, C = x->C;
+  x->O[0] = {Ly, Lx, false, false};
+  x->O[1] = {Ly, Lx, false, true};
+  x->O[2] = {Lx, Ly, true, false};
+  x->O[3] = {Lx, Ly, true, true};
+  x->Lmax = std::max(Ly, Lx);
+  x->S = (long long)x->chi * D * x->chi;
+  x->S4 = (long long)x->chi * D * D * x->chi;
+  x->SI = std::max((long long)D * D * D * x->chi * x->chi, std::max(x->S, (long long)D * D * x->chi * x->chi));
+  x->trivial_bond.assign(x->Lmax + 1, 1);
+  // original site offsets
+  long long off = 0, hoff = 0;
+  for (int k = 0; k < Ly; ++k)
+    for (int m = 0; m < Lx; ++m) {
+      const int sz = (m == 0 ? 1 : D) * (m == Lx - 1 ? 1 : D) * (k == 0 ? 1 : D) * (k == Ly - 1 ? 1 : D);
+      x->site_off.push_back(off);
+      x->site_half_off.push_back(hoff);
+      x->site_size.push_back(sz);
+      off += 2LL * sz;
+      hoff += sz;
+    }
+  x->P = off;
+  x->Ph = hoff;
+  x->sketch_host.assign(sketch, sketch + (size_t)x->Lmax * x->chi * D * x->chi);
+
+  cudaError_t e;
+#define ALLOC(p, n) if ((e = x->alloc(&(p), (size_t)(n))) != cudaSuccess) return x->fail(PEPSVMC_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e))
+  ALLOC(x->master, x->P);
+  ALLOC(x->grad, x->P);
+  ALLOC(x->sumG, x->P);
+  ALLOC(x->sumGE, x->P);
+  ALLOC(x->sums, 4);
+  ALLOC(x->spins, (long long)C * Ly * Lx);
+  ALLOC(x->ones, std::max(C, 1) + 1);
+  ALLOC(x->zeros_d, C);
+  for (int o = 0; o < 4; ++o) {
+    // permuted copies and their gather maps
+    const Orient& Ob = x->O[o];
+    std::vector<int> map_lurd(x->P), map_urld(x->P);
+    long long po = 0;
+    x->perm_site_off[o].clear();
+    for (int kp = 0; kp < Ob.Ly; ++kp)
+      for (int mp = 0; mp < Ob.Lx; ++mp) {
+        const int Dlp = mp == 0 ? 1 : D, Drp = mp == Ob.Lx - 1 ? 1 : D, Dup = kp == 0 ? 1 : D,
+                  Ddp = kp == Ob.Ly - 1 ? 1 : D;
+        int k, m;
+        x->orig(o, kp, mp, k, m);
+        const int Dl = m == 0 ? 1 : D, Dr = m == Lx - 1 ? 1 : D, Du = k == 0 ? 1 : D, Dd = k == Ly - 1 ? 1 : D;
+        const long long sz = (long long)Dlp * Drp * Dup * Ddp;
+        x->perm_site_off[o].push_back(po);
+        for (int s = 0; s < 2; ++s)
+          for (int lp = 0; lp < Dlp; ++lp)
+            for (int rp = 0; rp < Drp; ++rp)
+              for (int up = 0; up < Dup; ++up)
+                for (int dp = 0; dp < Ddp; ++dp) {
+                  int l, r, u, d;
+                  if (o == 0) { l = lp; r = rp; u = up; d = dp; }
+                  else if (o == 1) { l = lp; r = rp; u = dp; d = up; }
+                  else if (o == 2) { l = up; r = dp; u = lp; d = rp; }
+                  else { l = dp; r = up; u = lp; d = rp; }
+                  const long long src = x->site_off[(size_t)k * Lx + m] + s * sz + (((long long)l * Dr + r) * Du + u) * Dd + d;
+                  const long long i_lurd = po + s * sz + (((long long)lp * Dup + up) * Drp + rp) * Ddp + dp;
+                  const long long i_urld = po + s * sz + (((long long)up * Drp + rp) * Dlp + lp) * Ddp + dp;
+                  map_lurd[i_lurd] = (int)src;
+                  map_urld[i_urld] = (int)src;
+                }
+        po += 2 * sz;
+      }
+    for (int t = 0; t < 2; ++t) {
+      ALLOC(x->perm[o][t], x->P);
+      ALLOC(x->perm_map[o][t], x->P);
+      const std::vector<int>& mp = t == 0 ? map_lurd : map_urld;
+      if ((e = x->cps(x->perm_map[o][t], mp.data(), x->P * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return x->fail_cuda(e);
+    }
+  }
+  auto mkstore = [&](Store& s, int rows, int L, int nslots) -> int {
+    s.rows = rows;
+    s.L = L;
+    s.bond.assign(rows, std::vector<int>(L + 1, 1));
+    cudaError_t ee;
+    if ((ee = x->alloc(&s.base, (size_t)nslots * L * C * x->S)) != cudaSuccess)
+      return x->fail(PEPSVMC_ENOMEM, std::string("cudaMalloc failed (boundary MPS store): ") + cudaGetErrorString(ee));
+    if ((ee = x->alloc(&s.logs, (size_t)nslots * C)) != cudaSuccess) return x->fail(PEPSVMC_ENOMEM, "cudaMalloc failed");
+    return PEPSVMC_OK;
+  };
+  int rc;
+  if ((rc = mkstore(x->st_top, Ly, Lx, Ly)) != 0) return rc;
+  if ((rc = mkstore(x->st_bot, Ly, Lx, Ly)) != 0) return rc;
+  if ((rc = mkstore(x->st_colbot, Lx, Ly, Lx)) != 0) return rc;
+  if ((rc = mkstore(x->st_coltop, Lx, Ly, 2)) != 0) return rc;
+  const long long L1 = x->Lmax + 1;
+  ALLOC(x->envL, L1 * C * x->S);
+  ALLOC(x->envR, L1 * C * x->S);
+  ALLOC(x->envRf, L1 * C * x->S);
+  ALLOC(x->l3[0], C * x->S);
+  ALLOC(x->l3[1], C * x->S);
+  ALLOC(x->fl, C * x->S);
+  ALLOC(x->tmp1, C * x->SI);
+  ALLOC(x->tmp2, C * x->SI);
+  ALLOC(x->R4, (long long)(Lx + 1) * C * x->S4);
+  ALLOC(x->l4[0], C * x->S4);
+  ALLOC(x->l4[1], C * x->S4);
+  ALLOC(x->fl4, C * x->S4);
+  for (int i = 0; i < 2; ++i) {
+    ALLOC(x->ptop[i], C * x->S4);
+    ALLOC(x->pbot[i], C * x->S4);
+  }
+  ALLOC(x->G, C * x->Ph);
+  ALLOC(x->eloc, C);
+  ALLOC(x->den, C);
+  ALLOC(x->logpsi, C);
+  ALLOC(x->sign, C);
+  ALLOC(x->exps, C);
+  ALLOC(x->status, 1);
+  ALLOC(x->counters, 2);
+  // site tables for the gradient accumulation
+  {
+    std::vector<int> es(x->Ph), sp(Ly * Lx);
+    std::vector<long long> full(Ly * Lx);
+    for (int j = 0; j < Ly * Lx; ++j) {
+      for (int i = 0; i < x->site_size[j]; ++i) es[x->site_half_off[j] + i] = j;
+      sp[j] = j;
+      full[j] = x->site_off[j];
+    }
+    ALLOC(x->elem_site, x->Ph);
+    ALLOC(x->d_site_half_off, Ly * Lx);
+    ALLOC(x->d_site_full_off, Ly * Lx);
+    ALLOC(x->d_site_size, Ly * Lx);
+    ALLOC(x->d_site_spin, Ly * Lx);
+    if ((e = x->cps(x->elem_site, es.data(), es.size() * sizeof(int), cudaMemcpyHostToDevice)) ||
+        (e = x->cps(x->d_site_half_off, x->site_half_off.data(), Ly * Lx * sizeof(long long), cudaMemcpyHostToDevice)) ||
+        (e = x->cps(x->d_site_full_off, full.data(), Ly * Lx * sizeof(long long), cudaMemcpyHostToDevice)) ||
+        (e = x->cps(x->d_site_size, x->site_size.data(), Ly * Lx * sizeof(int), cudaMemcpyHostToDevice)) ||
+        (e = x->cps(x->d_site_spin, sp.data(), Ly * Lx * sizeof(int), cudaMemcpyHostToDevice)))
+      return x->fail_cuda(e);
+  }
+#undef ALLOC
+  if ((e = x->cps(x->master, tensors, x->P * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return x->fail_cuda(e);
+  if ((e = k_fill(x->ones, C + 1, 1.f, x->st)) != cudaSuccess) return x->fail_cuda(e);
+  if ((e = k_fill_d(x->zeros_d, C, 0.0, x->st)) != cudaSuccess) return x->fail_cuda(e);
+  if ((e = x->ms(x->status, 0, sizeof(unsigned))) != cudaSuccess) return x->fail_cuda(e);
+  if ((e = x->ms(x->counters, 0, 2 * sizeof(unsigned long long))) != cudaSuccess) return x->fail_cuda(e);
+  if ((e = x->refresh_perms()) != cudaSuccess) return x->fail_cuda(e);
+  // Neel start
+  std::vector<int8_t> neel((size_t)C * Ly * Lx);
+  for (int c = 0; c < C; ++c)
+    for (int k = 0; k < Ly; ++k)
+      for (int m = 0; m < Lx; ++m) neel[((size_t)c * Ly + k) * Lx + m] = ((k + m) % 2 == 0) ? 1 : -1;
+  if ((e = x->cps(x->spins, neel.data(), neel.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return x->fail_cuda(e);
+  if ((e = x->sync()) != cudaSuccess) return x->fail_cuda(e);
+  return PEPSVMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pepsvmc_init(const pepsvmc_config* cfg, const double* tensors, const double* sketch, void* stream,
+                 pepsvmc_ctx** out) {
+  if (!out) return PEPSVMC_EINVAL;
+  *out = nullptr;
+  std::string why;
+  int rc = validate(cfg, why);
+  pepsvmc_ctx* x = new (std::nothrow) pepsvmc_ctx();
+  if (!x) return PEPSVMC_ENOMEM;
+  *out = x;
+  if (rc != PEPSVMC_OK) return x->fail(rc, why);
+  if (!tensors || !sketch) return x->fail(PEPSVMC_EINVAL, "tensors and sketch must not be null");
+  x->cfg = *cfg;
+  x->st = (cudaStream_t)stream;
+  // PEPSVMC_DRY_RUN=1 (read once per process): no device is touched; every launch of
+  // the orchestration is bounds-checked on the host and skipped.  Validation tooling only.
+  static const bool dry_env = [] {
+    const char* v = getenv("PEPSVMC_DRY_RUN");
+    return v && v[0] == '1';
+  }();
+  g_dry_run = dry_env;
+  x->dry = dry_env;
+  x->C = cfg->n_chains;
+  x->Ly = cfg->Ly;
+  x->Lx = cfg->Lx;
+  x->D = cfg->D;
+  x->chi = cfg->chi;
+  x->nfit = cfg->n_fit;
+  return setup(x, tensors, sketch);
+}
+
+void pepsvmc_destroy(pepsvmc_ctx* x) {
+  if (!x) return;
+  if (!x->allocs.empty()) {
+    if (x->st) cudaStreamSynchronize(x->st);
+    else cudaDeviceSynchronize();  // NOLINT
+  }
+  for (void* p : x->allocs) cudaFree(p);
+  delete x;
+}
+
+const char* pepsvmc_last_error(const pepsvmc_ctx* x) { return x ? x->err.c_str() : "null context"; }
+int64_t pepsvmc_n_params(const pepsvmc_ctx* x) { return x ? x->P : 0; }
+int64_t pepsvmc_n_grad_entries(const pepsvmc_ctx* x) { return x ? x->Ph : 0; }
+int64_t pepsvmc_launch_count(const pepsvmc_ctx* x) { return x ? x->launches : 0; }
+
+int pepsvmc_set_spins(pepsvmc_ctx* x, const int8_t* s) {
+  if (!x || !s) return PEPSVMC_EINVAL;
+  const size_t n = (size_t)x->C * x->Ly * x->Lx;
+  for (size_t i = 0; i < n; ++i)
+    if (s[i] != 1 && s[i] != -1) return x->fail(PEPSVMC_EINVAL, "spins must be +1 or -1");
+  cudaError_t e = x->cp(x->spins, s, n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = x->sync();
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  x->top_valid = false;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_get_spins(pepsvmc_ctx* x, int8_t* s) {
+  if (!x || !s) return PEPSVMC_EINVAL;
+  cudaError_t e = x->cp(s, x->spins, (size_t)x->C * x->Ly * x->Lx, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = x->sync();
+  return e == cudaSuccess ? PEPSVMC_OK : x->fail_cuda(e);
+}
+
+int pepsvmc_set_tensors(pepsvmc_ctx* x, const double* t) {
+  if (!x || !t) return PEPSVMC_EINVAL;
+  cudaError_t e = x->cp(x->master, t, x->P * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = x->refresh_perms();
+  if (e == cudaSuccess) e = x->sync();
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  x->top_valid = false;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_get_tensors(pepsvmc_ctx* x, double* t) {
+  if (!x || !t) return PEPSVMC_EINVAL;
+  cudaError_t e = x->cp(t, x->master, x->P * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = x->sync();
+  return e == cudaSuccess ? PEPSVMC_OK : x->fail_cuda(e);
+}
+
+int pepsvmc_set_sweep_counter(pepsvmc_ctx* x, uint64_t s) {
+  if (!x) return PEPSVMC_EINVAL;
+  x->sweep_counter = s;
+  return PEPSVMC_OK;
+}
+uint64_t pepsvmc_get_sweep_counter(const pepsvmc_ctx* x) { return x ? x->sweep_counter : 0; }
+
+int pepsvmc_enable_trace(pepsvmc_ctx* x, int32_t on) {
+  if (!x) return PEPSVMC_EINVAL;
+  if (on && !x->trace_ratio) {
+    cudaError_t e;
+    if ((e = x->alloc(&x->trace_ratio, (size_t)x->C * x->nbonds())) != cudaSuccess ||
+        (e = x->alloc(&x->trace_dec, (size_t)x->C * x->nbonds())) != cudaSuccess)
+      return x->fail(PEPSVMC_ENOMEM, "trace allocation failed");
+  }
+  x->trace_on = on ? 1 : 0;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_get_trace(pepsvmc_ctx* x, double* ratio, int8_t* decision) {
+  if (!x) return PEPSVMC_EINVAL;
+  if (!x->trace_ratio) return x->fail(PEPSVMC_ESTATE, "trace not enabled");
+  const size_t n = (size_t)x->C * x->nbonds();
+  cudaError_t e = cudaSuccess;
+  if (ratio) e = x->cp(ratio, x->trace_ratio, n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && decision) e = x->cp(decision, x->trace_dec, n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = x->sync();
+  return e == cudaSuccess ? PEPSVMC_OK : x->fail_cuda(e);
+}
+
+int pepsvmc_sample_sweep(pepsvmc_ctx* x, int32_t n, double* rate) {
+  if (!x || n < 0) return PEPSVMC_EINVAL;
+  cudaError_t e = x->ms(x->counters, 0, 2 * sizeof(unsigned long long));
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = x->sweep_once();
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  int rc = x->check_status();
+  if (rc) return rc;
+  if (rate) {
+    unsigned long long h[2];
+    e = x->cps(h, x->counters, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return x->fail_cuda(e);
+    *rate = h[0] ? (double)h[1] / (double)h[0] : 0.0;
+  }
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_measure(pepsvmc_ctx* x, double* eloc, double* logpsi, int8_t* sign) {
+  if (!x) return PEPSVMC_EINVAL;
+  cudaError_t e = x->measure_dev();
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  int rc = x->check_status();
+  if (rc) return rc;
+  if (eloc && (e = x->cps(eloc, x->eloc, x->C * sizeof(double), cudaMemcpyDeviceToHost))) return x->fail_cuda(e);
+  if (logpsi && (e = x->cps(logpsi, x->logpsi, x->C * sizeof(double), cudaMemcpyDeviceToHost))) return x->fail_cuda(e);
+  if (sign && (e = x->cps(sign, x->sign, x->C, cudaMemcpyDeviceToHost))) return x->fail_cuda(e);
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_get_chain_grad(pepsvmc_ctx* x, int32_t chain, double* out) {
+  if (!x || !out || chain < 0 || chain >= x->C) return PEPSVMC_EINVAL;
+  if (!x->have_measure) return x->fail(PEPSVMC_ESTATE, "no measurement yet");
+  std::vector<float> h(x->Ph);
+  cudaError_t e = x->cps(h.data(), x->G + (long long)chain * x->Ph, x->Ph * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  for (long long i = 0; i < x->Ph; ++i) out[i] = h[i];
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_amplitude(pepsvmc_ctx* x, int32_t row, double* logpsi, int8_t* sign) {
+  if (!x || row < 0 || row >= x->Ly) return PEPSVMC_EINVAL;
+  cudaError_t e = x->amplitude_dev(row);
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  int rc = x->check_status();
+  if (rc) return rc;
+  if (logpsi && (e = x->cps(logpsi, x->logpsi, x->C * sizeof(double), cudaMemcpyDeviceToHost))) return x->fail_cuda(e);
+  if (sign && (e = x->cps(sign, x->sign, x->C, cudaMemcpyDeviceToHost))) return x->fail_cuda(e);
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_energy_and_grad(pepsvmc_ctx* x, int32_t n, double* E_mean, double* E_var, double* eloc,
+                            double* logpsi, int8_t* sign, double* grad) {
+  if (!x || n < 1) return PEPSVMC_EINVAL;
+  cudaError_t e = cudaSuccess;
+  if ((e = x->ms(x->sumG, 0, x->P * sizeof(double))) ||
+      (e = x->ms(x->sumGE, 0, x->P * sizeof(double))) ||
+      (e = x->ms(x->sums, 0, 4 * sizeof(double))) ||
+      (e = x->ms(x->counters, 0, 2 * sizeof(unsigned long long))))
+    return x->fail_cuda(e);
+  for (int t = 0; t < n; ++t) {
+    if ((e = x->sweep_once()) || (e = x->measure_dev())) return x->fail_cuda(e);
+    x->launches += 2;
+    if ((e = k_energy_accum(x->eloc, x->C, x->sums, x->st))) return x->fail_cuda(e);
+    if ((e = k_grad_accum(x->G, x->Ph, x->Ph, x->elem_site, x->d_site_half_off, x->d_site_full_off, x->d_site_size,
+                          x->d_site_spin, x->spins, (long long)x->Ly * x->Lx, x->eloc, x->C, x->sumG, x->sumGE,
+                          x->st)))
+      return x->fail_cuda(e);
+    if (eloc && (e = x->cp(eloc + (size_t)t * x->C, x->eloc, x->C * sizeof(double), cudaMemcpyDeviceToHost)))
+      return x->fail_cuda(e);
+    if (logpsi && (e = x->cp(logpsi + (size_t)t * x->C, x->logpsi, x->C * sizeof(double), cudaMemcpyDeviceToHost)))
+      return x->fail_cuda(e);
+    if (sign && (e = x->cp(sign + (size_t)t * x->C, x->sign, x->C, cudaMemcpyDeviceToHost)))
+      return x->fail_cuda(e);
+  }
+  ++x->launches;
+  if ((e = k_grad_final(x->sumG, x->sumGE, x->sums, x->P, x->grad, x->st))) return x->fail_cuda(e);
+  int rc = x->check_status();
+  if (rc) return rc;
+  x->have_grad = true;
+  double s[4];
+  if ((e = x->cps(s, x->sums, sizeof(s), cudaMemcpyDeviceToHost))) return x->fail_cuda(e);
+  const double mean = s[0] / s[2];
+  if (E_mean) *E_mean = mean;
+  if (E_var) *E_var = s[1] / s[2] - mean * mean;
+  if (grad && (e = x->cps(grad, x->grad, x->P * sizeof(double), cudaMemcpyDeviceToHost))) return x->fail_cuda(e);
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_update(pepsvmc_ctx* x, double delta, uint64_t step) {
+  if (!x) return PEPSVMC_EINVAL;
+  if (!x->have_grad) return x->fail(PEPSVMC_ESTATE, "no gradient: call pepsvmc_energy_and_grad first");
+  ++x->launches;
+  cudaError_t e = k_sgd(x->master, x->grad, x->P, delta, x->cfg.seed, step, x->st);
+  if (e == cudaSuccess) e = x->refresh_perms();
+  if (e == cudaSuccess) e = x->sync();
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  x->top_valid = false;
+  return PEPSVMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,416 @@
+// Per-chain kernels of the VMC-PEPS hot path (arXiv:1908.09359).
+//
+// Scaling: environments are rescaled by exact powers of two (the exponent of
+// their largest entry), so a rescaled environment differs from the unscaled
+// one by no rounding at all; exponents are summed per chain where a log
+// amplitude is needed.  Boundary MPSs are normalised by their 2-norm and the
+// log of the norm is carried in float64 (App. B keeps |U_k> bounded this way).
+#include "kernels.cuh"
+
+namespace pv {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double uniform24(unsigned w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  T tot = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+  return tot;
+}
+
+__device__ __forceinline__ float block_max(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float m = 0.f;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, red[i]);
+  return m;
+}
+
+__global__ void fill_kernel(float* p, long long n, float v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+__global__ void fill_d_kernel(double* p, long long n, double v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+__global__ void gather_kernel(float* dst, const double* src, const int* map, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[map[i]];
+}
+
+// Scale x (and x2, x3 by the same factor) by 2^-e, e the exponent of max|x|.
+__global__ void normalize_pow2_kernel(float* x, long long bs, int n, float* x2, long long bs2, int n2, float* x3,
+                                      long long bs3, int n3, int* exps, unsigned* status) {
+  __shared__ float red[kThreads / 32];
+  const int b = blockIdx.x;
+  float* xb = x + b * bs;
+  float mx = 0.f;
+  bool bad = false;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float v = xb[i];
+    if (!isfinite(v)) bad = true;
+    mx = fmaxf(mx, fabsf(v));
+  }
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
+    return;
+  }
+  mx = block_max(mx, red);
+  if (mx == 0.f) {
+    if (threadIdx.x == 0) atomicOr(status, ST_ZEROPSI);
+    return;
+  }
+  int e;
+  frexpf(mx, &e);
+  const float s = ldexpf(1.f, -e);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xb[i] *= s;
+  if (x2) {
+    float* p = x2 + b * bs2;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) p[i] *= s;
+  }
+  if (x3) {
+    float* p = x3 + b * bs3;
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) p[i] *= s;
+  }
+  if (exps && threadIdx.x == 0) exps[b] += e;
+}
+
+__global__ void mps_normalize_kernel(float* x, long long bs, int n, const int* exps, const double* log_in,
+                                     double* log_out, unsigned* status) {
+  __shared__ double red[kThreads / 32];
+  const int b = blockIdx.x;
+  float* xb = x + b * bs;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)xb[i] * xb[i];
+  s = block_sum(s, red);
+  if (!(s > 0.0) || !isfinite(s)) {
+    if (threadIdx.x == 0) atomicOr(status, isfinite(s) ? ST_ZEROPSI : ST_NONFINITE);
+    return;
+  }
+  const double nrm = sqrt(s);
+  const float inv = (float)(1.0 / nrm);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xb[i] *= inv;
+  if (threadIdx.x == 0) {
+    const double li = log_in ? log_in[b] : 0.0;
+    log_out[b] = li + log(nrm) + (exps ? exps[b] * 0.6931471805599453 : 0.0);
+  }
+}
+
+// Sequential Metropolis step on one pair (Eq. (9)) for every chain.
+__global__ void metropolis_kernel(const MetropolisArgs a) {
+  __shared__ double red[kThreads / 32];
+  __shared__ float redf[kThreads / 32];
+  __shared__ int acc_s;
+  const int b = blockIdx.x;
+  const float* cur = a.cur + b * a.bs_cur;
+  const float* Rc = a.Rcur + b * a.bs_Rcur;
+  const float* fl = a.flip + b * a.bs_flip;
+  const float* Rf = a.Rflip + b * a.bs_Rflip;
+  int8_t* sp = a.spins + b * a.spin_stride;
+  const bool anti = sp[a.site_a] != sp[a.site_b];
+  double den = 0.0, num = 0.0;
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x) den += (double)cur[i] * Rc[i];
+  den = block_sum(den, red);
+  if (anti) {
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) num += (double)fl[i] * Rf[i];
+    num = block_sum(num, red);
+  }
+  if (threadIdx.x == 0) {
+    int accept = 0;
+    if (den == 0.0) atomicOr(a.status, ST_ZEROPSI);
+    if (anti) {
+      double rho = 0.0;
+      if (den != 0.0) {
+        rho = num / den;
+        if (!isfinite(rho)) {
+          atomicOr(a.status, ST_NONFINITE);
+        } else {
+          const uint4 w = philox4x32_10(
+              make_uint4((unsigned)b, (unsigned)a.sweep, (unsigned)a.bond, kTagMetropolis),
+              make_uint2((unsigned)(a.key & 0xffffffffull), (unsigned)(a.key >> 32)));
+          const double u = uniform24(w.x);
+          const double p = fmin(1.0, rho * rho);
+          accept = (u < p) ? 1 : 0;
+        }
+      }
+      if (accept) {
+        sp[a.site_a] = (int8_t)-sp[a.site_a];
+        sp[a.site_b] = (int8_t)-sp[a.site_b];
+      }
+      atomicAdd(&a.counters[0], 1ull);
+      if (accept) atomicAdd(&a.counters[1], 1ull);
+      if (a.trace_ratio) a.trace_ratio[b * a.trace_stride + a.bond] = rho;
+      if (a.trace_dec) a.trace_dec[b * a.trace_stride + a.bond] = (int8_t)accept;
+    } else {
+      if (a.trace_ratio) a.trace_ratio[b * a.trace_stride + a.bond] = 0.0;
+      if (a.trace_dec) a.trace_dec[b * a.trace_stride + a.bond] = (int8_t)-1;
+    }
+    acc_s = accept;
+  }
+  __syncthreads();
+  const float* src = acc_s ? fl : cur;
+  float mx = 0.f;
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x) mx = fmaxf(mx, fabsf(src[i]));
+  mx = block_max(mx, redf);
+  float s = 1.f;
+  if (mx > 0.f && isfinite(mx)) {
+    int e;
+    frexpf(mx, &e);
+    s = ldexpf(1.f, -e);
+  }
+  float* out = a.out + b * a.bs_out;
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x) out[i] = src[i] * s;
+}
+
+__global__ void dot_kernel(const float* a, long long bsa, const float* bb, long long bsb, int n, double* out,
+                           unsigned* status) {
+  __shared__ double red[kThreads / 32];
+  const int b = blockIdx.x;
+  const float* x = a + b * bsa;
+  const float* y = bb + b * bsb;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)x[i] * y[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    out[b] = s;
+    if (s == 0.0) atomicOr(status, ST_ZEROPSI);
+    if (!isfinite(s)) atomicOr(status, ST_NONFINITE);
+  }
+}
+
+__global__ void ratio_accum_kernel(const float* a, long long bsa, const float* bb, long long bsb, int n,
+                                   const double* den, const int8_t* spins, long long spin_stride, int si, int sj,
+                                   double halfJ, double* eloc, unsigned* status) {
+  __shared__ double red[kThreads / 32];
+  const int b = blockIdx.x;
+  const int8_t* sp = spins + b * spin_stride;
+  if (sp[si] == sp[sj]) return;  // no off-diagonal element for a parallel pair
+  const float* x = a + b * bsa;
+  const float* y = bb + b * bsb;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)x[i] * y[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    const double r = s / den[b];
+    if (!isfinite(r)) atomicOr(status, ST_NONFINITE);
+    eloc[b] += halfJ * r;
+  }
+}
+
+__global__ void eloc_diag_kernel(const int8_t* spins, int Ly, int Lx, double J1, double J2, double* eloc,
+                                 int batch) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const int8_t* s = spins + (long long)b * Ly * Lx;
+  double e = 0.0;
+  for (int k = 0; k < Ly; ++k)
+    for (int m = 0; m < Lx; ++m) {
+      const int v = s[k * Lx + m];
+      if (m + 1 < Lx) e += J1 * 0.25 * v * s[k * Lx + m + 1];
+      if (k + 1 < Ly) e += J1 * 0.25 * v * s[(k + 1) * Lx + m];
+      if (J2 != 0.0 && k + 1 < Ly && m + 1 < Lx) {
+        e += J2 * 0.25 * v * s[(k + 1) * Lx + m + 1];
+        e += J2 * 0.25 * s[k * Lx + m + 1] * s[(k + 1) * Lx + m];
+      }
+    }
+  eloc[b] = e;
+}
+
+__global__ void logpsi_kernel(const float* x, long long bs, const int* exps, const double* logT, const double* logB,
+                              double* logpsi, int8_t* sign, int batch, unsigned* status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const float v = x[b * bs];
+  if (v == 0.f) atomicOr(status, ST_ZEROPSI);
+  logpsi[b] = logT[b] + logB[b] + exps[b] * 0.6931471805599453 + log(fabs((double)v));
+  sign[b] = v < 0.f ? (int8_t)-1 : (int8_t)1;
+}
+
+__global__ void grad_accum_kernel(const float* G, long long bsG, long long Ph, const int* elem_site,
+                                  const long long* site_half_off, const long long* site_full_off,
+                                  const int* site_size, const int* site_spin, const int8_t* spins,
+                                  long long spin_stride, const double* eloc, int batch, double* sumG,
+                                  double* sumGE) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= Ph) return;
+  const int j = elem_site[e];
+  const long long local = e - site_half_off[j];
+  const int si = site_spin[j];
+  double g0 = 0, g1 = 0, ge0 = 0, ge1 = 0;
+  for (int c = 0; c < batch; ++c) {
+    const double v = G[c * bsG + e];
+    const double E = eloc[c];
+    if (spins[c * spin_stride + si] > 0) {
+      g0 += v;
+      ge0 += v * E;
+    } else {
+      g1 += v;
+      ge1 += v * E;
+    }
+  }
+  const long long f0 = site_full_off[j] + local, f1 = f0 + site_size[j];
+  sumG[f0] += g0;
+  sumG[f1] += g1;
+  sumGE[f0] += ge0;
+  sumGE[f1] += ge1;
+}
+
+__global__ void energy_accum_kernel(const double* eloc, int batch, double* sums) {
+  __shared__ double red[kThreads / 32];
+  double s = 0, s2 = 0;
+  for (int i = threadIdx.x; i < batch; i += blockDim.x) {
+    s += eloc[i];
+    s2 += eloc[i] * eloc[i];
+  }
+  s = block_sum(s, red);
+  s2 = block_sum(s2, red);
+  if (threadIdx.x == 0) {
+    sums[0] += s;
+    sums[1] += s2;
+    sums[2] += batch;
+  }
+}
+
+__global__ void grad_final_kernel(const double* sumG, const double* sumGE, const double* sums, long long P,
+                                  double* grad) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const double n = sums[2];
+  const double E = sums[0] / n;
+  grad[i] = sumGE[i] / n - (sumG[i] / n) * E;
+}
+
+__global__ void sgd_kernel(double* master, const double* grad, long long P, double delta, unsigned long long key,
+                           unsigned long long step) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const uint4 w = philox4x32_10(make_uint4((unsigned)(i & 0xffffffffll), (unsigned)(i >> 32), (unsigned)step, kTagUpdate),
+                                make_uint2((unsigned)(key & 0xffffffffull), (unsigned)(key >> 32)));
+  const double r = uniform24(w.x);
+  const double g = grad[i];
+  const double sg = g > 0.0 ? 1.0 : (g < 0.0 ? -1.0 : 0.0);
+  master[i] -= r * delta * sg;
+}
+
+inline int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)(g > 1048576 ? 1048576 : (g < 1 ? 1 : g));
+}
+
+}  // namespace
+
+bool g_dry_run = false;
+
+cudaError_t k_fill(float* p, long long n, float v, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  fill_kernel<<<grid_for(n), 256, 0, st>>>(p, n, v);
+  return cudaGetLastError();
+}
+cudaError_t k_fill_d(double* p, long long n, double v, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  fill_d_kernel<<<grid_for(n), 256, 0, st>>>(p, n, v);
+  return cudaGetLastError();
+}
+cudaError_t k_gather_f32(float* dst, const double* src, const int* map, long long n, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  gather_kernel<<<grid_for(n), 256, 0, st>>>(dst, src, map, n);
+  return cudaGetLastError();
+}
+cudaError_t k_normalize_pow2(float* x, long long bs, int n, float* x2, long long bs2, int n2, float* x3,
+                             long long bs3, int n3, int* exps, int batch, unsigned* status, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  normalize_pow2_kernel<<<batch, kThreads, 0, st>>>(x, bs, n, x2, bs2, n2, x3, bs3, n3, exps, status);
+  return cudaGetLastError();
+}
+cudaError_t k_mps_normalize(float* x, long long bs, int n, const int* exps, const double* log_in, double* log_out,
+                            int batch, unsigned* status, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  mps_normalize_kernel<<<batch, kThreads, 0, st>>>(x, bs, n, exps, log_in, log_out, status);
+  return cudaGetLastError();
+}
+cudaError_t k_metropolis(const MetropolisArgs& a, int batch, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  metropolis_kernel<<<batch, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t k_dot(const float* a, long long bsa, const float* b, long long bsb, int n, double* out, int batch,
+                  unsigned* status, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  dot_kernel<<<batch, kThreads, 0, st>>>(a, bsa, b, bsb, n, out, status);
+  return cudaGetLastError();
+}
+cudaError_t k_ratio_accum(const float* a, long long bsa, const float* b, long long bsb, int n, const double* den,
+                          const int8_t* spins, long long spin_stride, int si, int sj, double halfJ, double* eloc,
+                          int batch, unsigned* status, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  ratio_accum_kernel<<<batch, kThreads, 0, st>>>(a, bsa, b, bsb, n, den, spins, spin_stride, si, sj, halfJ, eloc,
+                                                 status);
+  return cudaGetLastError();
+}
+cudaError_t k_eloc_diag(const int8_t* spins, int Ly, int Lx, double J1, double J2, double* eloc, int batch,
+                        cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  eloc_diag_kernel<<<(batch + 127) / 128, 128, 0, st>>>(spins, Ly, Lx, J1, J2, eloc, batch);
+  return cudaGetLastError();
+}
+cudaError_t k_logpsi(const float* x, long long bs, const int* exps, const double* logT, const double* logB,
+                     double* logpsi, int8_t* sign, int batch, unsigned* status, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  logpsi_kernel<<<(batch + 127) / 128, 128, 0, st>>>(x, bs, exps, logT, logB, logpsi, sign, batch, status);
+  return cudaGetLastError();
+}
+cudaError_t k_grad_accum(const float* G, long long bsG, long long Ph, const int* elem_site,
+                         const long long* site_half_off, const long long* site_full_off, const int* site_size,
+                         const int* site_spin, const int8_t* spins, long long spin_stride, const double* eloc,
+                         int batch, double* sumG, double* sumGE, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  grad_accum_kernel<<<(int)((Ph + 255) / 256), 256, 0, st>>>(G, bsG, Ph, elem_site, site_half_off, site_full_off,
+                                                             site_size, site_spin, spins, spin_stride, eloc, batch,
+                                                             sumG, sumGE);
+  return cudaGetLastError();
+}
+cudaError_t k_energy_accum(const double* eloc, int batch, double* sums, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  energy_accum_kernel<<<1, kThreads, 0, st>>>(eloc, batch, sums);
+  return cudaGetLastError();
+}
+cudaError_t k_grad_final(const double* sumG, const double* sumGE, const double* sums, long long P, double* grad,
+                         cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  grad_final_kernel<<<(int)((P + 255) / 256), 256, 0, st>>>(sumG, sumGE, sums, P, grad);
+  return cudaGetLastError();
+}
+cudaError_t k_sgd(double* master, const double* grad, long long P, double delta, unsigned long long key,
+                  unsigned long long step, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  sgd_kernel<<<(int)((P + 255) / 256), 256, 0, st>>>(master, grad, P, delta, key, step);
+  return cudaGetLastError();
+}
+
+}  // namespace pv

@@ -1,0 +1,52 @@
+"""Host logic of the CUDA engine, run without a GPU.
+
+With PEPSVMC_DRY_RUN=1 the library skips every device call but still walks the whole
+orchestration -- boundary-MPS fits in four lattice orientations, both sweep phases,
+the three- and four-line measurement, gradient accumulation and sign-SGD -- and
+checks the memory span of every launch against its allocation.  This runs each
+workload's full launch sequence in a subprocess (the mode is process-wide).
+"""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+from paper_1908_09359_gb300 import build, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+SCRIPT = r"""
+import json, sys
+import numpy as np
+from paper_1908_09359_gb300 import inputs, api
+w = inputs.WORKLOADS[sys.argv[1]]
+L = max(w["Ly"], w["Lx"])
+t = inputs.peps_tensors(w["Ly"], w["Lx"], w["D"], 1)
+sk = np.zeros((L, w["chi"], w["D"], w["chi"]))
+c = api.PepsVMC(w["Ly"], w["Lx"], w["D"], w["chi"], w["n_chains"], t, sk, J1=w["J1"], J2=w["J2"],
+                seed=1, n_fit=3, stream=0)
+n0 = c.launches
+c.sample_sweep(1)
+n1 = c.launches
+c.measure()
+n2 = c.launches
+c.amplitude(w["Ly"] // 2)
+c.energy_and_grad(1)
+c.update(0.01, 1)
+c.enable_trace(True)
+c.sample_sweep(1)
+print(json.dumps(dict(sweep=n1 - n0, measure=n2 - n1)))
+"""
+
+
+@pytest.mark.parametrize("name", list(inputs.WORKLOADS))
+def test_every_launch_in_bounds(name):
+    build.build()
+    env = dict(os.environ, PEPSVMC_DRY_RUN="1", PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", SCRIPT, name], capture_output=True, text=True, env=env,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    counts = json.loads(r.stdout.strip().splitlines()[-1])
+    assert counts["sweep"] > 0 and counts["measure"] > 0
