@@ -55,7 +55,8 @@ typedef struct {
   int32_t reserved[7];  /* must be zero                                    */
 } pepsvmc_config;
 
-/* Create a context.  Boundary-MPS truncation (App. B) is the variational fit
+/* Create a context (on failure *out may still receive a context that holds the
+ * error text; pass it to pepsvmc_destroy).  Boundary-MPS truncation (App. B) is the variational fit
  * of ||M|U> - |U'>||^2 by n_fit one-site half-sweeps; its starting guess is the
  * random MPS ``sketch``.
  *   tensors: host, packed layout above, float64, copied.
@@ -140,6 +141,14 @@ int pepsvmc_update(pepsvmc_ctx* ctx, double delta, uint64_t step);
 /* Kernel launches issued by this context since its creation (a counter kept by
  * the host side of the library). */
 int64_t pepsvmc_launch_count(const pepsvmc_ctx* ctx);
+
+/* Optional timing of every contraction and QR launch with CUDA events recorded
+ * on the context's stream (adds about a microsecond of host time per launch).
+ * pepsvmc_set_profiling resets the counters.  pepsvmc_get_profile fills out[6]:
+ * contraction launches, their algorithmic flops (2*M*N*K per chain), their
+ * summed device time in ms, QR launches, their device time in ms, 0.         */
+int pepsvmc_set_profiling(pepsvmc_ctx* ctx, int32_t on);
+int pepsvmc_get_profile(pepsvmc_ctx* ctx, double* out);
 
 #ifdef __cplusplus
 }

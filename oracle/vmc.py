@@ -35,6 +35,19 @@ import numpy as np
 
 from . import philox
 
+_PATHS = {}
+
+
+def _einsum(spec, *ops):
+    """np.einsum with a pairwise (greedy) contraction order and no cap on the size of
+    intermediates; the order of a sum changes nothing but rounding."""
+    key = (spec,) + tuple(o.shape for o in ops)
+    path = _PATHS.get(key)
+    if path is None:
+        path = np.einsum_path(spec, *ops, optimize=("greedy", 1e15))[0]
+        _PATHS[key] = path
+    return np.einsum(spec, *ops, optimize=path)
+
 # ----------------------------------------------------------------------------- lattice
 
 
@@ -145,22 +158,22 @@ def compress(X, chi, W, n_fit):
     R = [None] * (L + 1)
     R[L] = np.ones((1, 1))
     for m in range(L - 1, 0, -1):  # R[m]: (X bond left of m, V bond left of m)
-        R[m] = np.einsum("xpy,bpc,yc->xb", X[m], V[m], R[m + 1])
+        R[m] = _einsum("xpy,bpc,yc->xb", X[m], V[m], R[m + 1])
     Le = [None] * (L + 1)
     Le[0] = np.ones((1, 1))
     for sweep in range(n_fit):
         order = range(L) if sweep % 2 == 0 else range(L - 1, -1, -1)
         for m in order:
-            Y = np.einsum("xb,xpy,yc->bpc", Le[m], X[m], R[m + 1])  # optimal site m
+            Y = _einsum("xb,xpy,yc->bpc", Le[m], X[m], R[m + 1])  # optimal site m
             b0, p, b1 = Y.shape
             if sweep % 2 == 0 and m < L - 1:
                 Q, _ = qr_pos(Y.reshape(b0 * p, b1))
                 V[m] = Q.reshape(b0, p, b1)
-                Le[m + 1] = np.einsum("xb,xpy,bpc->yc", Le[m], X[m], V[m])
+                Le[m + 1] = _einsum("xb,xpy,bpc->yc", Le[m], X[m], V[m])
             elif sweep % 2 == 1 and m > 0:
                 Q, _ = qr_pos(Y.reshape(b0, p * b1).T)
                 V[m] = Q.T.reshape(b0, p, b1)
-                R[m] = np.einsum("xpy,bpc,yc->xb", X[m], V[m], R[m + 1])
+                R[m] = _einsum("xpy,bpc,yc->xb", X[m], V[m], R[m + 1])
             else:
                 V[m] = Y
     nrm = np.linalg.norm(V[L - 1])
@@ -200,21 +213,21 @@ def bottom_envs(grid, spins, chi, W, n_fit):
 
 def env3_left(E, T, a, B):
     """L(m) from L(m-1): columns of (T_k, row k, B_k) absorbed from the left."""
-    return np.einsum("xlb,xua,lrud,bdc->arc", E, T, a, B)
+    return _einsum("xlb,xua,lrud,bdc->arc", E, T, a, B)
 
 
 def env3_right(E, T, a, B):
     """R(m) from R(m+1)."""
-    return np.einsum("arc,xua,lrud,bdc->xlb", E, T, a, B)
+    return _einsum("arc,xua,lrud,bdc->xlb", E, T, a, B)
 
 
 def env4_left(E, T, a1, a2, B):
     """Four-line left environment of rows (k, k+1): E[a, l1, l2, b]."""
-    return np.einsum("xpqb,xua,prud,qsde,bec->arsc", E, T, a1, a2, B)
+    return _einsum("xpqb,xua,prud,qsde,bec->arsc", E, T, a1, a2, B)
 
 
 def env4_right(E, T, a1, a2, B):
-    return np.einsum("arsc,xua,prud,qsde,bec->xpqb", E, T, a1, a2, B)
+    return _einsum("arsc,xua,prud,qsde,bec->xpqb", E, T, a1, a2, B)
 
 
 def _normalised(E):
@@ -248,38 +261,46 @@ def _row_phase(grid, spins, chi, W, n_fit, seed, chain, sweep, bond_base, trace)
     Ts, logT = [trivial_mps(Lx)], [0.0]
     for k in range(Ly):
         T, B = Ts[k], Bs[k]
-        a = grid[k]
-        R = [None] * (Lx + 1)
-        Rf = [None] * (Lx + 1)
-        R[Lx] = np.ones((1, 1, 1))
-        for m in range(Lx - 1, 0, -1):
-            s = sidx(spins[k, m])
-            raw = env3_right(R[m + 1], T[m], a[m][s], B[m])
-            nrm = np.linalg.norm(raw)
-            R[m] = raw / nrm
-            Rf[m] = env3_right(R[m + 1], T[m], a[m][1 - s], B[m]) / nrm
-        E = np.ones((1, 1, 1))
-        for m in range(Lx - 1):
-            s = sidx(spins[k, m])
-            cur = env3_left(E, T[m], a[m][s], B[m])
-            if spins[k, m] != spins[k, m + 1]:
-                flip = env3_left(E, T[m], a[m][1 - s], B[m])
-                rho = float(np.vdot(flip, Rf[m + 1]) / np.vdot(cur, R[m + 1]))
-                bond = bond_base + k * (Lx - 1) + m
-                u = philox.metropolis_uniform(seed, chain, sweep, bond)
-                accept = u < min(1.0, rho * rho)
-                if trace is not None:
-                    accept = trace.decide(bond, rho, u, accept)
-                if accept:
-                    spins[k, m] = -spins[k, m]
-                    spins[k, m + 1] = -spins[k, m + 1]
-                    cur = flip
-            E, _ = _normalised(cur)
+        _sample_row(grid, spins, k, T, B, seed, chain, sweep, bond_base, trace)
         if k < Ly - 1:
             V, ln = compress(mpo_times_mps(T, row_tensors(grid, spins, k)), chi, W, n_fit)
             Ts.append(V)
             logT.append(logT[-1] + ln)
     return Ts, logT
+
+
+def _sample_row(grid, spins, k, T, B, seed, chain, sweep, bond_base, trace):
+    """Metropolis visits of the horizontal bonds of row k, left to right, with the
+    fixed environments T_k, B_k; the left three-line environment follows the
+    accepted configuration (App. C, Fig. "contraction")."""
+    Lx = spins.shape[1]
+    a = grid[k]
+    R = [None] * (Lx + 1)
+    Rf = [None] * (Lx + 1)
+    R[Lx] = np.ones((1, 1, 1))
+    for m in range(Lx - 1, 0, -1):
+        s = sidx(spins[k, m])
+        raw = env3_right(R[m + 1], T[m], a[m][s], B[m])
+        nrm = np.linalg.norm(raw)
+        R[m] = raw / nrm
+        Rf[m] = env3_right(R[m + 1], T[m], a[m][1 - s], B[m]) / nrm
+    E = np.ones((1, 1, 1))
+    for m in range(Lx - 1):
+        s = sidx(spins[k, m])
+        cur = env3_left(E, T[m], a[m][s], B[m])
+        if spins[k, m] != spins[k, m + 1]:
+            flip = env3_left(E, T[m], a[m][1 - s], B[m])
+            rho = float(np.vdot(flip, Rf[m + 1]) / np.vdot(cur, R[m + 1]))
+            bond = bond_base + k * (Lx - 1) + m
+            u = philox.metropolis_uniform(seed, chain, sweep, bond)
+            accept = u < min(1.0, rho * rho)
+            if trace is not None:
+                accept = trace.decide(bond, rho, u, accept)
+            if accept:
+                spins[k, m] = -spins[k, m]
+                spins[k, m + 1] = -spins[k, m + 1]
+                cur = flip
+        E, _ = _normalised(cur)
 
 
 class Trace:
@@ -337,40 +358,47 @@ def measure(grid, spins, chi, W, n_fit, J1, J2, Ts=None, logT=None, want_grad=Tr
     G = [[None] * Lx for _ in range(Ly)]
     logpsi = sign = None
     for k in range(Ly):
-        T, B = Ts[k], Bs[k]
-        row = row_tensors(grid, spins, k)
         if k == Ly // 2:
-            logpsi, sign = row_psi(T, row, B, logT[k], logB[k])
-        R = [None] * (Lx + 1)
-        Rf = [None] * (Lx + 1)
-        R[Lx] = np.ones((1, 1, 1))
-        for m in range(Lx - 1, 0, -1):
-            s = sidx(spins[k, m])
-            raw = env3_right(R[m + 1], T[m], grid[k][m][s], B[m])
-            nrm = np.linalg.norm(raw)
-            R[m] = raw / nrm
-            Rf[m] = env3_right(R[m + 1], T[m], grid[k][m][1 - s], B[m]) / nrm
-        E = np.ones((1, 1, 1))
-        for m in range(Lx):
-            s = sidx(spins[k, m])
-            cur = env3_left(E, T[m], grid[k][m][s], B[m])
-            if want_grad:
-                psi_km = np.vdot(cur, R[m + 1])   # Tr[L0(m) R0(m+1)], same scale as Delta
-                delta = np.einsum("xlb,xua,bdc,arc->lrud", E, T[m], B[m], R[m + 1])
-                G[k][m] = delta / psi_km
-            if m < Lx - 1:
-                sg = spins[k, m] * spins[k, m + 1]
-                e += J1 * sg / 4.0
-                scale[0] += abs(J1) / 4.0
-                if sg < 0:
-                    flip = env3_left(E, T[m], grid[k][m][1 - s], B[m])
-                    t = 0.5 * J1 * float(np.vdot(flip, Rf[m + 1]) / np.vdot(cur, R[m + 1]))
-                    e += t
-                    scale[0] += abs(t)
-            E, _ = _normalised(cur)
+            logpsi, sign = row_psi(Ts[k], row_tensors(grid, spins, k), Bs[k], logT[k], logB[k])
+        e += _row_terms(grid, spins, k, Ts[k], Bs[k], J1, G if want_grad else None, scale)
     for k in range(Ly - 1):
         e += _pair_terms(grid, spins, k, Ts[k], Bs[k + 1], J1, J2, scale)
     return dict(eloc=e, logpsi=logpsi, sign=sign, G=G if want_grad else None, eloc_scale=scale[0])
+
+
+def _row_terms(grid, spins, k, T, B, J1, G, scale):
+    """Horizontal NN terms of row k from its three-line environments (App. C, Fig.
+    "contraction"); fills G[k][m] = Delta/Psi when G is given."""
+    Lx = spins.shape[1]
+    R = [None] * (Lx + 1)
+    Rf = [None] * (Lx + 1)
+    R[Lx] = np.ones((1, 1, 1))
+    for m in range(Lx - 1, 0, -1):
+        s = sidx(spins[k, m])
+        raw = env3_right(R[m + 1], T[m], grid[k][m][s], B[m])
+        nrm = np.linalg.norm(raw)
+        R[m] = raw / nrm
+        Rf[m] = env3_right(R[m + 1], T[m], grid[k][m][1 - s], B[m]) / nrm
+    e = 0.0
+    E = np.ones((1, 1, 1))
+    for m in range(Lx):
+        s = sidx(spins[k, m])
+        cur = env3_left(E, T[m], grid[k][m][s], B[m])
+        if G is not None:
+            psi_km = np.vdot(cur, R[m + 1])   # Tr[L0(m) R0(m+1)], same scale as Delta
+            delta = _einsum("xlb,xua,bdc,arc->lrud", E, T[m], B[m], R[m + 1])
+            G[k][m] = delta / psi_km
+        if m < Lx - 1:
+            sg = spins[k, m] * spins[k, m + 1]
+            e += J1 * sg / 4.0
+            scale[0] += abs(J1) / 4.0
+            if sg < 0:
+                flip = env3_left(E, T[m], grid[k][m][1 - s], B[m])
+                t = 0.5 * J1 * float(np.vdot(flip, Rf[m + 1]) / np.vdot(cur, R[m + 1]))
+                e += t
+                scale[0] += abs(t)
+        E, _ = _normalised(cur)
+    return e
 
 
 def _col(grid, spins, k, m, flip_top=False, flip_bot=False):

@@ -157,5 +157,14 @@ class PepsVMC:
                                                      _dp(el), _dp(lp), _i8(sg), _dp(gr)))
         return dict(E_mean=Em.value, E_var=Ev.value, eloc=el, logpsi=lp, sign=sg, grad=gr)
 
+    def set_profiling(self, on=True):
+        self._check(self.lib.pepsvmc_set_profiling(self.ctx, 1 if on else 0))
+
+    def get_profile(self):
+        out = np.zeros(6)
+        self._check(self.lib.pepsvmc_get_profile(self.ctx, _dp(out)))
+        return dict(gemm_launches=int(out[0]), gemm_flops=out[1], gemm_ms=out[2],
+                    qr_launches=int(out[3]), qr_ms=out[4])
+
     def update(self, delta, step):
         self._check(self.lib.pepsvmc_update(self.ctx, float(delta), int(step)))

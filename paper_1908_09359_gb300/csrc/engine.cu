@@ -219,6 +219,48 @@ struct pepsvmc_ctx {
     return (long long)((M - 1) / c23) * s1 + (long long)(c2 - 1) * s2 + (long long)(c3 - 1) * s3;
   }
 
+  // ----------------------------------------------- optional per-launch event timing
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Pending { cudaEvent_t a, b; int kind; };
+  std::vector<Pending> pending;
+  double prof_acc[6] = {0, 0, 0, 0, 0, 0};  // gemm launches, gemm flops, gemm ms, qr launches, qr ms, -
+
+  cudaEvent_t ev() {
+    if (ev_pool.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      return e;
+    }
+    cudaEvent_t e = ev_pool.back();
+    ev_pool.pop_back();
+    return e;
+  }
+  cudaError_t collect() {
+    if (pending.empty() || dry) return cudaSuccess;
+    PV_CUDA(cudaEventSynchronize(pending.back().b));
+    for (const Pending& p : pending) {
+      float ms = 0.f;
+      PV_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+      prof_acc[p.kind == 0 ? 2 : 4] += ms;
+      ev_pool.push_back(p.a);
+      ev_pool.push_back(p.b);
+    }
+    pending.clear();
+    return cudaSuccess;
+  }
+  template <typename F>
+  cudaError_t timed(int kind, F&& launch) {
+    if (!prof || dry) return launch();
+    cudaEvent_t a = ev(), b = ev();
+    PV_CUDA(cudaEventRecord(a, st));
+    PV_CUDA(launch());
+    PV_CUDA(cudaEventRecord(b, st));
+    pending.push_back({a, b, kind});
+    if (pending.size() >= 16384) return collect();
+    return cudaSuccess;
+  }
+
   cudaError_t gemm(GemmDesc& g) {
     g.batch = C;
     if (g.M % (g.cm2 * g.cm3) || g.N % (g.cn2 * g.cn3)) {
@@ -235,7 +277,11 @@ struct pepsvmc_ctx {
         (g.inv_scale && !span(g.inv_scale, b1, 8, "gemm scale")))
       return cudaErrorInvalidValue;
     ++launches;
-    return gemm_f32(g, gemm_f32_pick(g), st);
+    if (prof) {
+      prof_acc[0] += 1;
+      prof_acc[1] += 2.0 * g.M * g.N * g.K * (double)C;
+    }
+    return timed(0, [&] { return gemm_f32(g, gemm_f32_pick(g), st); });
   }
 
   cudaError_t qr(const float* Y, long long bsY, long long yrs, long long ycs, float* Q, long long bsQ, long long qrs,
@@ -249,7 +295,8 @@ struct pepsvmc_ctx {
       return cudaErrorInvalidValue;
     }
     ++launches;
-    return qr_pos_batched(Y, bsY, yrs, ycs, Q, bsQ, qrs, qcs, rows, cols, batch, st);
+    if (prof) prof_acc[3] += 1;
+    return timed(1, [&] { return qr_pos_batched(Y, bsY, yrs, ycs, Q, bsQ, qrs, qcs, rows, cols, batch, st); });
   }
 
   // Per-chain array span: chains 0..C-1 with stride bs, n entries each.
@@ -1087,6 +1134,8 @@ void pepsvmc_destroy(pepsvmc_ctx* x) {
     if (x->st) cudaStreamSynchronize(x->st);
     else cudaDeviceSynchronize();  // NOLINT
   }
+  x->collect();
+  for (cudaEvent_t e : x->ev_pool) cudaEventDestroy(e);
   for (void* p : x->allocs) cudaFree(p);
   delete x;
 }
@@ -1095,6 +1144,23 @@ const char* pepsvmc_last_error(const pepsvmc_ctx* x) { return x ? x->err.c_str()
 int64_t pepsvmc_n_params(const pepsvmc_ctx* x) { return x ? x->P : 0; }
 int64_t pepsvmc_n_grad_entries(const pepsvmc_ctx* x) { return x ? x->Ph : 0; }
 int64_t pepsvmc_launch_count(const pepsvmc_ctx* x) { return x ? x->launches : 0; }
+
+int pepsvmc_set_profiling(pepsvmc_ctx* x, int32_t on) {
+  if (!x) return PEPSVMC_EINVAL;
+  cudaError_t e = x->collect();
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  for (double& v : x->prof_acc) v = 0.0;
+  x->prof = on != 0;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_get_profile(pepsvmc_ctx* x, double* out) {
+  if (!x || !out) return PEPSVMC_EINVAL;
+  cudaError_t e = x->collect();
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  for (int i = 0; i < 6; ++i) out[i] = x->prof_acc[i];
+  return PEPSVMC_OK;
+}
 
 int pepsvmc_set_spins(pepsvmc_ctx* x, const int8_t* s) {
   if (!x || !s) return PEPSVMC_EINVAL;

@@ -50,13 +50,25 @@ def n_params(Ly: int, Lx: int, D: int) -> int:
     return int(sum(np.prod(site_shape(Ly, Lx, D, k, m)) for k in range(Ly) for m in range(Lx)))
 
 
-def peps_tensors(Ly: int, Lx: int, D: int, seed: int, normalise: bool = False) -> np.ndarray:
-    """Flat float64 array, site-major (k, then m), each site (s, l, r, u, d) row-major."""
+def peps_tensors(Ly: int, Lx: int, D: int, seed: int, normalise: bool = False,
+                 bond_decay: float = 0.0) -> np.ndarray:
+    """Flat float64 array, site-major (k, then m), each site (s, l, r, u, d) row-major.
+
+    ``bond_decay`` > 0 scales virtual index i of every leg by exp(-bond_decay * i / 2),
+    i.e. bond weights lambda_i = exp(-bond_decay * i) split evenly between the two
+    tensors of a bond, as after a simple-update initialisation (App. A absorbs
+    lambda^(1/2) into each tensor).  0 gives the plain iid N(0,1) tensors.
+    """
     rng = np.random.default_rng(seed)
     parts = []
     for k in range(Ly):
         for m in range(Lx):
-            t = rng.standard_normal(site_shape(Ly, Lx, D, k, m))
+            shp = site_shape(Ly, Lx, D, k, m)
+            t = rng.standard_normal(shp)
+            if bond_decay > 0.0:
+                for axis in range(1, 5):
+                    w = np.exp(-bond_decay * np.arange(shp[axis]) / 2.0)
+                    t = t * w.reshape([-1 if a == axis else 1 for a in range(5)])
             if normalise:
                 t = t / np.sqrt(np.sum(t * t))
             parts.append(t.ravel())
