@@ -138,6 +138,24 @@ int pepsvmc_energy_and_grad(pepsvmc_ctx* ctx, int32_t n_sweeps, double* E_mean, 
  * Errors: ESTATE if no gradient was computed.                               */
 int pepsvmc_update(pepsvmc_ctx* ctx, double delta, uint64_t step);
 
+/* Three-line environment step (App. C, Fig. "contraction" (c)) for n_chains chains,
+ * on the context's stream, with the context's scratch:
+ *   out[c](a',r,b') = sum over a,l,b,u,d of
+ *       E[c](a,l,b) * T[c](a,u,a') * A_{s_c}(l,r,u,d) * B[c](b,d,b')
+ * E: left environment (cT, Dl, cB); T: top boundary-MPS site (cT, Du, cT2);
+ * B: bottom boundary-MPS site (cB, Dd, cB2); out: (cT2, Dr, cB2).  All are float32
+ * device arrays, row-major per chain, chains back to back (chain stride = size).
+ * A: the site tensor, float32 device array of both spin slots, each slot in the
+ * order (l, u, r, d); chain c uses slot 1 when spins[c] < 0 (int8 device array of
+ * n_chains), slot 0 otherwise or when spins is NULL.  Asynchronous on the stream.
+ * Errors: EINVAL for null pointers, non-positive sizes, n_chains above the
+ * context's chains or bonds whose intermediates exceed the context's scratch
+ * (Dl*cB*Du*cT2 and cB*cT2*Dr*Dd must not exceed D^3*chi^2); ECUDA.          */
+int pepsvmc_env3_left(pepsvmc_ctx* ctx, const float* E, const float* T, const float* A,
+                      const int8_t* spins, const float* B, float* out, int32_t n_chains,
+                      int32_t cT, int32_t cB, int32_t cT2, int32_t cB2,
+                      int32_t Dl, int32_t Dr, int32_t Du, int32_t Dd);
+
 /* Kernel launches issued by this context since its creation (a counter kept by
  * the host side of the library). */
 int64_t pepsvmc_launch_count(const pepsvmc_ctx* ctx);

@@ -24,7 +24,7 @@ SYMBOLS = [
     "pepsvmc_set_sweep_counter", "pepsvmc_get_sweep_counter", "pepsvmc_sample_sweep",
     "pepsvmc_enable_trace", "pepsvmc_get_trace", "pepsvmc_measure", "pepsvmc_n_grad_entries",
     "pepsvmc_get_chain_grad", "pepsvmc_amplitude", "pepsvmc_energy_and_grad", "pepsvmc_update",
-    "pepsvmc_launch_count", "pepsvmc_set_profiling", "pepsvmc_get_profile",
+    "pepsvmc_launch_count", "pepsvmc_set_profiling", "pepsvmc_get_profile", "pepsvmc_env3_left",
 ]
 
 
@@ -79,6 +79,7 @@ def load(path: str | None = None):
         "pepsvmc_launch_count": (I64, [P]),
         "pepsvmc_set_profiling": (C.c_int, [P, I32]),
         "pepsvmc_get_profile": (C.c_int, [P, D]),
+        "pepsvmc_env3_left": (C.c_int, [P, P, P, P, P, P, P] + [I32] * 9),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -166,5 +166,13 @@ class PepsVMC:
         return dict(gemm_launches=int(out[0]), gemm_flops=out[1], gemm_ms=out[2],
                     qr_launches=int(out[3]), qr_ms=out[4])
 
+    def env3_left(self, E, T, A, spins, B, out, dims):
+        """Three-line environment step on device tensors (torch CUDA tensors or raw
+        pointers); ``dims`` = (n_chains, cT, cB, cT2, cB2, Dl, Dr, Du, Dd)."""
+        ptr = lambda t: C.c_void_p(t if isinstance(t, int) else (t.data_ptr() if t is not None else 0))  # noqa: E731
+        self._check(self.lib.pepsvmc_env3_left(self.ctx, ptr(E), ptr(T), ptr(A), ptr(spins), ptr(B), ptr(out),
+                                               *[int(v) for v in dims]))
+
     def update(self, delta, step):
         self._check(self.lib.pepsvmc_update(self.ctx, float(delta), int(step)))
+

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "pepsvmc.h"
+#include "stages.cuh"
 
 using namespace pv;
 
@@ -341,29 +342,11 @@ struct pepsvmc_ctx {
   cudaError_t left3(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
                     const SiteOp& a, int flip, const float* B, long long bsB, int cB2, float* out,
                     long long bsO) {
-    const int Dl = a.Dl, Dr = a.Dr, Du = a.Du, Dd = a.Dd;
-    GemmDesc g;
-    g.M = Dl * cB; g.N = Du * cT2; g.K = cT;
-    g.A = E; g.sAm = 1; g.sAk = (long long)Dl * cB; g.bsA = bsE;
-    g.B = T; g.sBk = (long long)Du * cT2; g.sBn = 1; g.bsB = bsT;
-    g.C = tmp1; g.bsC = SI;
-    g.cm2 = cB; g.sCm1 = Du; g.sCm2 = (long long)cT2 * Dl * Du;
-    g.cn2 = cT2; g.sCn1 = 1; g.sCn2 = (long long)Dl * Du;
-    PV_CUDA(gemm(g));
-    GemmDesc h;
-    h.M = cB * cT2; h.N = Dr * Dd; h.K = Dl * Du;
-    h.A = tmp1; h.sAm = (long long)Dl * Du; h.sAk = 1; h.bsA = SI;
-    sel(h, a, a.lurd, flip); h.sBk = (long long)Dr * Dd; h.sBn = 1;
-    h.C = tmp2; h.bsC = SI;
-    h.cm2 = cT2; h.sCm1 = Dd; h.sCm2 = (long long)Dr * cB * Dd;
-    h.cn2 = Dd; h.sCn1 = (long long)cB * Dd; h.sCn2 = 1;
-    PV_CUDA(gemm(h));
-    GemmDesc q;
-    q.M = cT2 * Dr; q.N = cB2; q.K = cB * Dd;
-    q.A = tmp2; q.sAm = (long long)cB * Dd; q.sAk = 1; q.bsA = SI;
-    q.B = B; q.sBk = cB2; q.sBn = 1; q.bsB = bsB;
-    q.C = out; q.bsC = bsO; q.sCm1 = cB2; q.sCn1 = 1;
-    return gemm(q);
+    GemmDesc g[3];
+    env3_left_descs(g, Env3Dims{cT, cB, cT2, cB2, a.Dl, a.Dr, a.Du, a.Dd}, E, bsE, T, bsT, a.lurd, a.size,
+                    spins + a.spin, (long long)Ly * Lx, flip, B, bsB, out, bsO, tmp1, tmp2, SI);
+    for (int i = 0; i < 3; ++i) PV_CUDA(gemm(g[i]));
+    return cudaSuccess;
   }
 
   // Three-line right step: E (cT2,Dr,cB2) -> out (cT,Dl,cB).
@@ -1144,6 +1127,27 @@ const char* pepsvmc_last_error(const pepsvmc_ctx* x) { return x ? x->err.c_str()
 int64_t pepsvmc_n_params(const pepsvmc_ctx* x) { return x ? x->P : 0; }
 int64_t pepsvmc_n_grad_entries(const pepsvmc_ctx* x) { return x ? x->Ph : 0; }
 int64_t pepsvmc_launch_count(const pepsvmc_ctx* x) { return x ? x->launches : 0; }
+
+int pepsvmc_env3_left(pepsvmc_ctx* x, const float* E, const float* T, const float* A, const int8_t* spins,
+                      const float* B, float* out, int32_t n_chains, int32_t cT, int32_t cB, int32_t cT2, int32_t cB2,
+                      int32_t Dl, int32_t Dr, int32_t Du, int32_t Dd) {
+  if (!x) return PEPSVMC_EINVAL;
+  const Env3Dims d{cT, cB, cT2, cB2, Dl, Dr, Du, Dd};
+  if (!E || !T || !A || !B || !out || n_chains < 1 || !env3_dims_ok(d))
+    return x->fail(PEPSVMC_EINVAL, "env3_left: null pointer or non-positive size");
+  if (n_chains > x->C || env3_scratch(d) > x->SI)
+    return x->fail(PEPSVMC_EINVAL, "env3_left: more chains or larger bonds than the context was created for");
+  GemmDesc g[3];
+  env3_left_descs(g, d, E, (long long)cT * Dl * cB, T, (long long)cT * Du * cT2, A, (long long)Dl * Dr * Du * Dd,
+                  spins, 1, 0, B, (long long)cB * Dd * cB2, out, (long long)cT2 * Dr * cB2, x->tmp1, x->tmp2, x->SI);
+  for (int i = 0; i < 3; ++i) {
+    g[i].batch = n_chains;
+    ++x->launches;
+    cudaError_t e = gemm_f32(g[i], gemm_f32_pick(g[i]), x->st);
+    if (e != cudaSuccess) return x->fail_cuda(e);
+  }
+  return PEPSVMC_OK;
+}
 
 int pepsvmc_set_profiling(pepsvmc_ctx* x, int32_t on) {
   if (!x) return PEPSVMC_EINVAL;

@@ -1,0 +1,55 @@
+"""Microbenchmarks of single hot-path launches at a workload's bulk shapes.
+
+    python -m paper_1908_09359_gb300.kernel_cases env3 --workload peps_24x24 [--chains N] [--reps R]
+
+``env3`` runs the three-line environment step (App. C) through the C ABI
+(pepsvmc_env3_left) with bulk bond dimensions (all boundary bonds = Dc), the shape
+that dominates the sweep; it prints the device time per step and the achieved
+algorithmic FLOP/s (2 * (2 Dc^3 D^2 + Dc^2 D^4) per chain).  These are the small,
+bounded cases that ncu captures use.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+
+def main():
+    import torch
+
+    from . import api, inputs
+    p = argparse.ArgumentParser()
+    p.add_argument("case", choices=["env3"])
+    p.add_argument("--workload", default="peps_24x24")
+    p.add_argument("--chains", type=int, default=None)
+    p.add_argument("--reps", type=int, default=10)
+    a = p.parse_args()
+    w = inputs.workload(a.workload, n_chains=1)
+    n = a.chains or inputs.WORKLOADS[a.workload]["n_chains"]
+    D, chi = w["D"], w["chi"]
+    ctx = api.PepsVMC(w["Ly"], w["Lx"], D, chi, n, w["tensors"], w["sketch"], seed=1)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    r = lambda *s: torch.randn(*s, generator=g, device="cuda")  # noqa: E731
+    E, T, B = r(n, chi, D, chi), r(n, chi, D, chi), r(n, chi, D, chi)
+    A = r(2, D, D, D, D)
+    spins = torch.where(torch.rand(n, generator=g, device="cuda") < 0.5, 1, -1).to(torch.int8)
+    out = torch.empty(n, chi, D, chi, device="cuda")
+    dims = (n, chi, chi, chi, chi, D, D, D, D)
+    for _ in range(3):
+        ctx.env3_left(E, T, A, spins, B, out, dims)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.reps):
+        ctx.env3_left(E, T, A, spins, B, out, dims)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    flops = 2.0 * (2 * chi ** 3 * D ** 2 + chi ** 2 * D ** 4) * n
+    print(json.dumps({"case": a.case, "workload": a.workload, "chains": n, "ms_per_step": ms,
+                      "tflops": flops / (ms / 1e3) / 1e12}))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
