@@ -156,6 +156,31 @@ int pepsvmc_env3_left(pepsvmc_ctx* ctx, const float* E, const float* T, const fl
                       int32_t cT, int32_t cB, int32_t cT2, int32_t cB2,
                       int32_t Dl, int32_t Dr, int32_t Du, int32_t Dd);
 
+/* pepsvmc_env3_left without a context and without allocating anything (the paper
+ * has no counterpart; this is a library convenience).  For callers that cannot
+ * call cudaMalloc where they need the step -- e.g. a service that reserved all of
+ * its device memory at start-up and must not allocate later, since cudaMalloc can
+ * synchronise the device and fragments a planned pool.  Same operation, layouts
+ * and spin rule as pepsvmc_env3_left; runs asynchronously on ``stream`` (a
+ * cudaStream_t, NULL = legacy default stream) on the current device.
+ * Scratch: the two intermediates live in one fixed array of
+ * PEPSVMC_NOALLOC_SCRATCH_FLOATS floats (16 MiB) of the library's own device
+ * memory, present on every GPU where the library's device code is loaded until
+ * the process exits.  The first call on a device looks up that array's device
+ * address (with the device current); make that first call before any stream
+ * capture.  Every call uses the same array, and it keeps the last call's
+ * contents (nothing in it needs to start at zero); calls whose execution overlaps
+ * on the GPU -- on different streams or devices sharing nothing, or from several
+ * host threads -- race on it and must be serialised by the caller.
+ * Errors: EINVAL for null pointers, non-positive sizes, or when
+ * 2 * n_chains * max(Dl*cB*Du*cT2, cB*cT2*Dr*Dd) exceeds the array; ECUDA.      */
+#define PEPSVMC_NOALLOC_SCRATCH_FLOATS 4194304
+int pepsvmc_env3_left_noalloc(const float* E, const float* T, const float* A,
+                              const int8_t* spins, const float* B, float* out,
+                              int32_t n_chains, int32_t cT, int32_t cB, int32_t cT2,
+                              int32_t cB2, int32_t Dl, int32_t Dr, int32_t Du, int32_t Dd,
+                              void* stream);
+
 /* Kernel launches issued by this context since its creation (a counter kept by
  * the host side of the library). */
 int64_t pepsvmc_launch_count(const pepsvmc_ctx* ctx);

@@ -14,6 +14,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libpepsvmc.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EZEROPSI, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 FP32, MIXED_BF16 = 0, 1
 
+NOALLOC_SCRATCH_FLOATS = 4194304  # PEPSVMC_NOALLOC_SCRATCH_FLOATS
+
 ERRORS = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
           ENONFINITE: "ENONFINITE", EZEROPSI: "EZEROPSI", ESTATE: "ESTATE"}
 
@@ -25,6 +27,7 @@ SYMBOLS = [
     "pepsvmc_enable_trace", "pepsvmc_get_trace", "pepsvmc_measure", "pepsvmc_n_grad_entries",
     "pepsvmc_get_chain_grad", "pepsvmc_amplitude", "pepsvmc_energy_and_grad", "pepsvmc_update",
     "pepsvmc_launch_count", "pepsvmc_set_profiling", "pepsvmc_get_profile", "pepsvmc_env3_left",
+    "pepsvmc_env3_left_noalloc",
 ]
 
 
@@ -80,6 +83,7 @@ def load(path: str | None = None):
         "pepsvmc_set_profiling": (C.c_int, [P, I32]),
         "pepsvmc_get_profile": (C.c_int, [P, D]),
         "pepsvmc_env3_left": (C.c_int, [P, P, P, P, P, P, P] + [I32] * 9),
+        "pepsvmc_env3_left_noalloc": (C.c_int, [P, P, P, P, P, P] + [I32] * 9 + [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -176,3 +176,19 @@ class PepsVMC:
     def update(self, delta, step):
         self._check(self.lib.pepsvmc_update(self.ctx, float(delta), int(step)))
 
+
+def env3_left_noalloc(E, T, A, spins, B, out, dims, stream=None):
+    """The three-line environment step without a context and without any device
+    allocation (for callers that must not allocate once running); the intermediates
+    use the library's fixed scratch array, so calls must not overlap on the GPU.
+    Arguments as PepsVMC.env3_left; ``stream`` defaults to torch's current stream."""
+    lib = _lib.load()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    ptr = lambda t: C.c_void_p(t if isinstance(t, int) else (t.data_ptr() if t is not None else 0))  # noqa: E731
+    rc = lib.pepsvmc_env3_left_noalloc(ptr(E), ptr(T), ptr(A), ptr(spins), ptr(B), ptr(out),
+                                       *[int(v) for v in dims], C.c_void_p(stream))
+    if rc != 0:
+        raise PepsvmcError(rc, "pepsvmc_env3_left_noalloc failed (sizes beyond the fixed scratch, "
+                               "null pointers or a CUDA error)")
