@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="peps_24x24")
     p.add_argument("--n-fit", type=int, default=3)
+    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "tf32", "bf16x3"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -192,8 +193,9 @@ def run_ours(args):
     w = inputs.workload(args.workload)
     C = w["n_chains"]
     spins = inputs.start_spins(C, w["Ly"], w["Lx"], w["seed"] + 7919 * rank, "random")
+    prec = api.PRECISIONS[args.precision]
     ctx = api.PepsVMC(w["Ly"], w["Lx"], w["D"], w["chi"], C, w["tensors"], w["sketch"], J1=w["J1"],
-                      J2=w["J2"], seed=w["seed"] + rank, n_fit=args.n_fit)
+                      J2=w["J2"], seed=w["seed"] + rank, n_fit=args.n_fit, precision=prec)
     ctx.set_spins(spins)
     delta = 1e-3
 
@@ -268,11 +270,28 @@ def run_ours(args):
         return
     achieved = prof["gemm_flops"] / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else None
     step_ms = ms / args.steps
+    if args.precision == "fp32":
+        kname, bound, peak = "gemm_f32_kernel (batched contraction, FP32 CUDA cores)", "alu", FP32_ALU_PEAK_TFLOPS
+        psrc = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        bf16 = peaks.get("bf16_tflops_sustained")
+        src = "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+        if bf16 is None:
+            bf16, src = 1700.0, "fallback sustained bf16 1.7 PFLOP/s (of fallback)"
+        # TF32 dense rate is half the BF16 rate (nominal 1.1 vs 2.25 PFLOP/s)
+        # TF32 dense rate is half the BF16 rate; split BF16 issues three BF16 MMAs per
+        # product, so its algorithmic flops are reported against a third of the BF16 peak
+        peak = {"bf16": bf16, "tf32": bf16 / 2.0, "bf16x3": bf16 / 3.0}[args.precision]
+        kname = ("gemm_tc_kernel (batched contraction, tcgen05 "
+                 + {"bf16": "kind::f16", "tf32": "kind::tf32", "bf16x3": "kind::f16, split hi+lo, 3 MMAs"}[
+                     args.precision] + ")")
+        bound = "tensor"
+        psrc = src + {"bf16": "", "tf32": " x 1/2 for TF32", "bf16x3": " x 1/3 for three BF16 MMAs"}[args.precision]
     roofline = {
-        "kernel": "gemm_f32_kernel (batched contraction, FP32 CUDA cores)",
-        "bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved / FP32_ALU_PEAK_TFLOPS if achieved else None,
-        "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
+        "kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "frac": achieved / peak if achieved else None, "peak_source": psrc,
         "traffic": None,
         "share_of_step": (prof["gemm_ms"] / args.steps) / step_ms,
         "launches": prof["gemm_launches"],
@@ -285,11 +304,14 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 operands, f32 accumulate",
+                                      "tf32": "tf32 operands, f32 accumulate",
+                                      "bf16x3": "bf16 hi+lo operands, f32 accumulate"}[args.precision],
         "data": "synthetic (seeded iid N(0,1) PEPS tensors, random S^z=0 starts)",
         "config": {"workload": args.workload, "Ly": w["Ly"], "Lx": w["Lx"], "D": w["D"], "Dc": w["chi"],
                    "J1": w["J1"], "J2": w["J2"], "chains_per_gpu": C, "n_fit": args.n_fit,
-                   "form": "plain FP32", "step": "sweep + measure + gradient sums + sign-SGD",
+                   "form": {"fp32": "plain FP32", "bf16": "mixed BF16 (tcgen05)", "tf32": "mixed TF32 (tcgen05)",
+                            "bf16x3": "mixed split-BF16 (tcgen05)"}[args.precision], "step": "sweep + measure + gradient sums + sign-SGD",
                    "l2": "working set (boundary-MPS caches, GBs) larger than L2; no flush"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),

@@ -39,7 +39,13 @@ enum {
   PEPSVMC_ESTATE = -7       /* call out of order (e.g. no measurement yet)   */
 };
 
-enum { PEPSVMC_FP32 = 0, PEPSVMC_MIXED_BF16 = 1 };
+/* Precision of the contractions: FP32 on CUDA cores; or, on the tcgen05 tensor
+ * cores with FP32 accumulation, operands rounded to BF16 (MIXED_BF16), to TF32
+ * (MIXED_TF32), or split into two BF16 parts x = hi + lo with three products per
+ * step (MIXED_BF16X3, close to FP32 accuracy).  In every mode the truncation QR, the
+ * ratios (float64 dot products), log amplitudes and the energy / gradient sums are
+ * as in FP32 mode.                                                              */
+enum { PEPSVMC_FP32 = 0, PEPSVMC_MIXED_BF16 = 1, PEPSVMC_MIXED_TF32 = 2, PEPSVMC_MIXED_BF16X3 = 3 };
 
 typedef struct pepsvmc_ctx pepsvmc_ctx;
 
@@ -51,7 +57,7 @@ typedef struct {
   int32_t n_fit;        /* one-site fit half-sweeps per truncation, odd    */
   double J1, J2;        /* NN and NNN couplings; J2 = 0 is Heisenberg      */
   uint64_t seed;        /* Philox key for Metropolis and sign-SGD uniforms */
-  int32_t precision;    /* PEPSVMC_FP32 or PEPSVMC_MIXED_BF16              */
+  int32_t precision;    /* PEPSVMC_FP32 or one of the PEPSVMC_MIXED_* modes  */
   int32_t reserved[7];  /* must be zero                                    */
 } pepsvmc_config;
 
@@ -192,6 +198,10 @@ int64_t pepsvmc_launch_count(const pepsvmc_ctx* ctx);
  * summed device time in ms, QR launches, their device time in ms, 0.         */
 int pepsvmc_set_profiling(pepsvmc_ctx* ctx, int32_t on);
 int pepsvmc_get_profile(pepsvmc_ctx* ctx, double* out);
+/* The same counters per launch shape, as JSON text written to buf (len bytes):
+ * [{"shape": "gemm tc M.. N.. K..", "launches": n, "flops": f, "ms": t}, ...].
+ * EINVAL if the text does not fit.                                          */
+int pepsvmc_get_profile_shapes(pepsvmc_ctx* ctx, char* buf, int64_t len);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libpepsvmc.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EZEROPSI, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
-FP32, MIXED_BF16 = 0, 1
+FP32, MIXED_BF16, MIXED_TF32, MIXED_BF16X3 = 0, 1, 2, 3
 
 NOALLOC_SCRATCH_FLOATS = 4194304  # PEPSVMC_NOALLOC_SCRATCH_FLOATS
 
@@ -27,7 +27,7 @@ SYMBOLS = [
     "pepsvmc_enable_trace", "pepsvmc_get_trace", "pepsvmc_measure", "pepsvmc_n_grad_entries",
     "pepsvmc_get_chain_grad", "pepsvmc_amplitude", "pepsvmc_energy_and_grad", "pepsvmc_update",
     "pepsvmc_launch_count", "pepsvmc_set_profiling", "pepsvmc_get_profile", "pepsvmc_env3_left",
-    "pepsvmc_env3_left_noalloc",
+    "pepsvmc_env3_left_noalloc", "pepsvmc_get_profile_shapes",
 ]
 
 
@@ -84,6 +84,7 @@ def load(path: str | None = None):
         "pepsvmc_get_profile": (C.c_int, [P, D]),
         "pepsvmc_env3_left": (C.c_int, [P, P, P, P, P, P, P] + [I32] * 9),
         "pepsvmc_env3_left_noalloc": (C.c_int, [P, P, P, P, P, P] + [I32] * 9 + [P]),
+        "pepsvmc_get_profile_shapes": (C.c_int, [P, C.c_char_p, I64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

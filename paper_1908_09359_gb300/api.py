@@ -10,7 +10,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import FP32, MIXED_BF16, PepsvmcError  # noqa: F401
+from ._lib import FP32, MIXED_BF16, MIXED_BF16X3, MIXED_TF32, PepsvmcError  # noqa: F401
 
 
 def _dp(a):
@@ -19,6 +19,9 @@ def _dp(a):
 
 def _i8(a):
     return a.ctypes.data_as(C.POINTER(C.c_int8)) if a is not None else None
+
+
+PRECISIONS = {"fp32": FP32, "bf16": MIXED_BF16, "tf32": MIXED_TF32, "bf16x3": MIXED_BF16X3}
 
 
 class PepsVMC:
@@ -172,6 +175,12 @@ class PepsVMC:
         ptr = lambda t: C.c_void_p(t if isinstance(t, int) else (t.data_ptr() if t is not None else 0))  # noqa: E731
         self._check(self.lib.pepsvmc_env3_left(self.ctx, ptr(E), ptr(T), ptr(A), ptr(spins), ptr(B), ptr(out),
                                                *[int(v) for v in dims]))
+
+    def get_profile_shapes(self):
+        import json
+        buf = C.create_string_buffer(1 << 20)
+        self._check(self.lib.pepsvmc_get_profile_shapes(self.ctx, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def update(self, delta, step):
         self._check(self.lib.pepsvmc_update(self.ctx, float(delta), int(step)))

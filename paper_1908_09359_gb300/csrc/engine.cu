@@ -223,7 +223,9 @@ struct pepsvmc_ctx {
   // ----------------------------------------------- optional per-launch event timing
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
-  struct Pending { cudaEvent_t a, b; int kind; };
+  struct Pending { cudaEvent_t a, b; int kind; std::string shape; double flops; };
+  struct ShapeStat { long long n = 0; double flops = 0, ms = 0; };
+  std::map<std::string, ShapeStat> shape_stats;
   std::vector<Pending> pending;
   double prof_acc[6] = {0, 0, 0, 0, 0, 0};  // gemm launches, gemm flops, gemm ms, qr launches, qr ms, -
 
@@ -244,6 +246,10 @@ struct pepsvmc_ctx {
       float ms = 0.f;
       PV_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
       prof_acc[p.kind == 0 ? 2 : 4] += ms;
+      ShapeStat& ss = shape_stats[p.shape];
+      ss.n += 1;
+      ss.flops += p.flops;
+      ss.ms += ms;
       ev_pool.push_back(p.a);
       ev_pool.push_back(p.b);
     }
@@ -251,13 +257,13 @@ struct pepsvmc_ctx {
     return cudaSuccess;
   }
   template <typename F>
-  cudaError_t timed(int kind, F&& launch) {
+  cudaError_t timed(int kind, F&& launch, const std::string& shape = "", double flops = 0.0) {
     if (!prof || dry) return launch();
     cudaEvent_t a = ev(), b = ev();
     PV_CUDA(cudaEventRecord(a, st));
     PV_CUDA(launch());
     PV_CUDA(cudaEventRecord(b, st));
-    pending.push_back({a, b, kind});
+    pending.push_back({a, b, kind, shape, flops});
     if (pending.size() >= 16384) return collect();
     return cudaSuccess;
   }
@@ -282,8 +288,29 @@ struct pepsvmc_ctx {
       prof_acc[0] += 1;
       prof_acc[1] += 2.0 * g.M * g.N * g.K * (double)C;
     }
-    return timed(0, [&] { return gemm_f32(g, gemm_f32_pick(g), st); });
+    if (!prof) return launch_gemm(g);
+    char key[96];
+    snprintf(key, sizeof(key), "gemm %s M%d N%d K%d", tc_route(g) ? "tc" : "f32", g.M, g.N, g.K);
+    return timed(0, [&] { return launch_gemm(g); }, key, 2.0 * g.M * g.N * g.K * (double)C);
   }
+
+  // Tensor cores for contractions big enough to fill a 128-row tile, CUDA cores otherwise.
+  int tc_mode() const {
+    switch (cfg.precision) {
+      case PEPSVMC_MIXED_BF16: return 2;
+      case PEPSVMC_MIXED_BF16X3: return 3;
+      case PEPSVMC_MIXED_TF32: return 4;
+      default: return 0;
+    }
+  }
+  bool tc_route(const GemmDesc& g) const {
+    return tc_mode() && (long long)g.M * g.N * g.K >= kTcMinWork && g.M >= 64 && g.K >= 8;
+  }
+  cudaError_t launch_gemm(const GemmDesc& g) {
+    if (tc_route(g)) return gemm_tc(g, tc_mode(), status, st);
+    return gemm_f32(g, gemm_f32_pick(g), st);
+  }
+  static constexpr long long kTcMinWork = 1 << 15;
 
   cudaError_t qr(const float* Y, long long bsY, long long yrs, long long ycs, float* Q, long long bsQ, long long qrs,
                  long long qcs, int rows, int cols, int batch) {
@@ -297,7 +324,10 @@ struct pepsvmc_ctx {
     }
     ++launches;
     if (prof) prof_acc[3] += 1;
-    return timed(1, [&] { return qr_pos_batched(Y, bsY, yrs, ycs, Q, bsQ, qrs, qcs, rows, cols, batch, st); });
+    char key[64];
+    snprintf(key, sizeof(key), "qr %dx%d", rows, cols);
+    return timed(1, [&] { return qr_pos_batched(Y, bsY, yrs, ycs, Q, bsQ, qrs, qcs, rows, cols, batch, st); },
+                 key, 0.0);
   }
 
   // Per-chain array span: chains 0..C-1 with stride bs, n entries each.
@@ -914,8 +944,11 @@ int validate(const pepsvmc_config* c, std::string& why) {
   if ((long long)c->chi * c->chi * c->D * 2 * 4 > 200 * 1024) { why = "chi*chi*D too large for the QR kernel"; return PEPSVMC_EINVAL; }
   if (c->n_chains < 1 || c->n_chains > (1 << 20)) { why = "n_chains must be >= 1"; return PEPSVMC_EINVAL; }
   if (c->n_fit < 1 || c->n_fit % 2 == 0) { why = "n_fit must be odd and >= 1"; return PEPSVMC_EINVAL; }
-  if (c->precision != PEPSVMC_FP32 && c->precision != PEPSVMC_MIXED_BF16) { why = "unknown precision"; return PEPSVMC_EINVAL; }
-  if (c->precision == PEPSVMC_MIXED_BF16) { why = "precision MIXED_BF16 is not built in this library"; return PEPSVMC_EINVAL; }
+  if (c->precision != PEPSVMC_FP32 && c->precision != PEPSVMC_MIXED_BF16 && c->precision != PEPSVMC_MIXED_TF32 &&
+      c->precision != PEPSVMC_MIXED_BF16X3) {
+    why = "unknown precision";
+    return PEPSVMC_EINVAL;
+  }
   for (int i = 0; i < 7; ++i)
     if (c->reserved[i]) { why = "reserved fields must be zero"; return PEPSVMC_EINVAL; }
   return PEPSVMC_OK;
@@ -1143,7 +1176,7 @@ int pepsvmc_env3_left(pepsvmc_ctx* x, const float* E, const float* T, const floa
   for (int i = 0; i < 3; ++i) {
     g[i].batch = n_chains;
     ++x->launches;
-    cudaError_t e = gemm_f32(g[i], gemm_f32_pick(g[i]), x->st);
+    cudaError_t e = x->launch_gemm(g[i]);
     if (e != cudaSuccess) return x->fail_cuda(e);
   }
   return PEPSVMC_OK;
@@ -1154,7 +1187,25 @@ int pepsvmc_set_profiling(pepsvmc_ctx* x, int32_t on) {
   cudaError_t e = x->collect();
   if (e != cudaSuccess) return x->fail_cuda(e);
   for (double& v : x->prof_acc) v = 0.0;
+  x->shape_stats.clear();
   x->prof = on != 0;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_get_profile_shapes(pepsvmc_ctx* x, char* buf, int64_t len) {
+  if (!x || !buf || len < 2) return PEPSVMC_EINVAL;
+  cudaError_t e = x->collect();
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  std::string js = "[";
+  for (const auto& kv : x->shape_stats) {
+    char row[256];
+    snprintf(row, sizeof(row), "%s{\"shape\":\"%s\",\"launches\":%lld,\"flops\":%.6g,\"ms\":%.6g}",
+             js.size() > 1 ? "," : "", kv.first.c_str(), kv.second.n, kv.second.flops, kv.second.ms);
+    js += row;
+  }
+  js += "]";
+  if ((int64_t)js.size() + 1 > len) return x->fail(PEPSVMC_EINVAL, "profile text longer than the buffer");
+  memcpy(buf, js.c_str(), js.size() + 1);
   return PEPSVMC_OK;
 }
 
