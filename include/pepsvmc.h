@@ -203,6 +203,21 @@ int pepsvmc_get_profile(pepsvmc_ctx* ctx, double* out);
  * EINVAL if the text does not fit.                                          */
 int pepsvmc_get_profile_shapes(pepsvmc_ctx* ctx, char* buf, int64_t len);
 
+/* Autotuner (on by default): the first launch of every contraction shape times each
+ * candidate kernel (six FP32 tile shapes; in the tensor-core modes also the TC tile
+ * widths 32/64/128/256) with CUDA events and keeps the fastest for this context.
+ * pepsvmc_set_autotune(ctx, 0) turns it off and forgets the choices (fixed
+ * heuristics then); pepsvmc_get_tuning writes the choices as JSON text:
+ * [{"shape": "...", "choice": "f32_cfg3" | "tc_bn64", "candidate_ms": [...]}, ...]. */
+int pepsvmc_set_autotune(pepsvmc_ctx* ctx, int32_t on);
+
+/* CUDA graphs (on by default): pepsvmc_energy_and_grad runs its first sample step
+ * (sweep + measurement + sums) eagerly, then captures the step's launches once into
+ * a CUDA graph on an internal stream and replays it for every later step (not while
+ * tracing or profiling).  pepsvmc_set_graphs(ctx, 0) runs every step eagerly.     */
+int pepsvmc_set_graphs(pepsvmc_ctx* ctx, int32_t on);
+int pepsvmc_get_tuning(pepsvmc_ctx* ctx, char* buf, int64_t len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,8 @@ SYMBOLS = [
     "pepsvmc_enable_trace", "pepsvmc_get_trace", "pepsvmc_measure", "pepsvmc_n_grad_entries",
     "pepsvmc_get_chain_grad", "pepsvmc_amplitude", "pepsvmc_energy_and_grad", "pepsvmc_update",
     "pepsvmc_launch_count", "pepsvmc_set_profiling", "pepsvmc_get_profile", "pepsvmc_env3_left",
-    "pepsvmc_env3_left_noalloc", "pepsvmc_get_profile_shapes",
+    "pepsvmc_env3_left_noalloc", "pepsvmc_get_profile_shapes", "pepsvmc_set_autotune", "pepsvmc_get_tuning",
+    "pepsvmc_set_graphs",
 ]
 
 
@@ -85,6 +86,9 @@ def load(path: str | None = None):
         "pepsvmc_env3_left": (C.c_int, [P, P, P, P, P, P, P] + [I32] * 9),
         "pepsvmc_env3_left_noalloc": (C.c_int, [P, P, P, P, P, P] + [I32] * 9 + [P]),
         "pepsvmc_get_profile_shapes": (C.c_int, [P, C.c_char_p, I64]),
+        "pepsvmc_set_autotune": (C.c_int, [P, I32]),
+        "pepsvmc_set_graphs": (C.c_int, [P, I32]),
+        "pepsvmc_get_tuning": (C.c_int, [P, C.c_char_p, I64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

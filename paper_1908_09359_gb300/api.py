@@ -182,6 +182,18 @@ class PepsVMC:
         self._check(self.lib.pepsvmc_get_profile_shapes(self.ctx, buf, len(buf)))
         return json.loads(buf.value.decode())
 
+    def set_graphs(self, on=True):
+        self._check(self.lib.pepsvmc_set_graphs(self.ctx, 1 if on else 0))
+
+    def set_autotune(self, on=True):
+        self._check(self.lib.pepsvmc_set_autotune(self.ctx, 1 if on else 0))
+
+    def get_tuning(self):
+        import json
+        buf = C.create_string_buffer(1 << 22)
+        self._check(self.lib.pepsvmc_get_tuning(self.ctx, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
     def update(self, delta, step):
         self._check(self.lib.pepsvmc_update(self.ctx, float(delta), int(step)))
 

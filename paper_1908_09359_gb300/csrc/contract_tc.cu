@@ -403,8 +403,8 @@ cudaError_t launch(const GemmDesc& d, unsigned* status, cudaStream_t st) {
 }
 
 template <int EB, bool X3>
-cudaError_t launch_bn(const GemmDesc& d, unsigned* status, cudaStream_t st) {
-  const int bn = d.N <= 32 ? 32 : d.N <= 64 ? 64 : d.N <= 128 ? 128 : 256;
+cudaError_t launch_bn(const GemmDesc& d, int bn, unsigned* status, cudaStream_t st) {
+  if (bn <= 0) bn = d.N <= 32 ? 32 : d.N <= 64 ? 64 : d.N <= 128 ? 128 : 256;
   switch (bn) {
     case 32: return launch<EB, 32, X3>(d, status, st);
     case 64: return launch<EB, 64, X3>(d, status, st);
@@ -419,11 +419,13 @@ cudaError_t launch_bn(const GemmDesc& d, unsigned* status, cudaStream_t st) {
 // BN = 32/64/128/256, so at most 5/4/3/2 CTAs share an SM and their tensor memory
 // (BN columns each) never exceeds the SM's 512 columns: allocation never waits.
 // mode: 2 = BF16, 3 = split BF16 (hi + lo), 4 = TF32.
-cudaError_t gemm_tc(const GemmDesc& d, int mode, unsigned* status, cudaStream_t st) {
+// bn: tile width 32/64/128/256, or 0 for the smallest that covers N.
+cudaError_t gemm_tc(const GemmDesc& d, int mode, int bn, unsigned* status, cudaStream_t st) {
   if (g_dry_run || d.M <= 0 || d.N <= 0 || d.batch <= 0) return cudaSuccess;
-  if (mode == 2) return launch_bn<2, false>(d, status, st);
-  if (mode == 3) return launch_bn<2, true>(d, status, st);
-  return launch_bn<4, false>(d, status, st);
+  if (bn != 0 && bn != 32 && bn != 64 && bn != 128 && bn != 256) return cudaErrorInvalidValue;
+  if (mode == 2) return launch_bn<2, false>(d, bn, status, st);
+  if (mode == 3) return launch_bn<2, true>(d, bn, status, st);
+  return launch_bn<4, false>(d, bn, status, st);
 }
 
 }  // namespace pv

@@ -125,6 +125,7 @@ struct pepsvmc_ctx {
   int* exps = nullptr;
   unsigned* status = nullptr;
   unsigned long long* counters = nullptr;
+  unsigned long long* d_sweep = nullptr;
   double* trace_ratio = nullptr;
   int8_t* trace_dec = nullptr;
   int* elem_site = nullptr;
@@ -304,10 +305,74 @@ struct pepsvmc_ctx {
     }
   }
   bool tc_route(const GemmDesc& g) const {
+    const auto it = tuned.find(tune_key(g));
+    if (it != tuned.end()) return it->second >= 100;
     return tc_mode() && (long long)g.M * g.N * g.K >= kTcMinWork && g.M >= 64 && g.K >= 8;
   }
+
+  // ---------------------------------------------------------------- autotuner
+  // Per contraction shape (dims, strides, scatter), every candidate kernel -- the six
+  // FP32 tile shapes and, in the tensor-core modes, the four TC tile widths -- is timed
+  // once with CUDA events on its first use; the fastest is kept for the context.
+  // Candidates compute the same product, so the timing runs are harmless.
+  bool autotune = true;
+  bool capturing = false;
+  std::map<std::string, int> tuned;               // choice: f32 config, or 100 + TC tile width
+  std::map<std::string, std::vector<float>> tune_ms;
+
+  static std::string tune_key(const GemmDesc& g) {
+    char k[320];
+    snprintf(k, sizeof(k), "%d %d %d|%lld %lld|%lld %lld %d|%d %d %lld %lld %lld|%d %d %lld %lld %lld", g.M, g.N, g.K,
+             g.sAm, g.sAk, g.sBk, g.sBn, g.sel != nullptr, g.cm2, g.cm3, g.sCm1, g.sCm2, g.sCm3, g.cn2, g.cn3, g.sCn1,
+             g.sCn2, g.sCn3);
+    return k;
+  }
+  cudaError_t run_choice(const GemmDesc& g, int choice) {
+    if (choice >= 100) return gemm_tc(g, tc_mode(), choice - 100, status, st);
+    return gemm_f32(g, choice, st);
+  }
+  cudaError_t tune(const GemmDesc& g, const std::string& key) {
+    std::vector<int> cand;
+    for (int c = 0; c < gemm_f32_num_configs(); ++c) cand.push_back(c);
+    if (tc_mode() && g.K >= 8)
+      for (int bn : {32, 64, 128, 256})
+        if (bn / 2 < g.N || bn == 32) cand.push_back(100 + bn);
+    cudaEvent_t e0 = ev(), e1 = ev();
+    int best = -1;
+    float best_ms = 0.f;
+    std::vector<float> times;
+    for (int c : cand) {
+      PV_CUDA(run_choice(g, c));  // warm
+      PV_CUDA(cudaEventRecord(e0, st));
+      PV_CUDA(run_choice(g, c));
+      PV_CUDA(cudaEventRecord(e1, st));
+      PV_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      PV_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      times.push_back(ms);
+      if (best < 0 || ms < best_ms) {
+        best = c;
+        best_ms = ms;
+      }
+    }
+    ev_pool.push_back(e0);
+    ev_pool.push_back(e1);
+    tuned[key] = best;
+    tune_ms[key] = times;
+    return cudaSuccess;
+  }
   cudaError_t launch_gemm(const GemmDesc& g) {
-    if (tc_route(g)) return gemm_tc(g, tc_mode(), status, st);
+    if (!dry && (autotune || !tuned.empty())) {
+      const std::string key = tune_key(g);
+      auto it = tuned.find(key);
+      if (it == tuned.end() && autotune && !capturing && !g.accumulate) {
+        PV_CUDA(tune(g, key));
+        it = tuned.find(key);
+      }
+      if (it != tuned.end()) return run_choice(g, it->second);
+    }
+    if (tc_mode() && (long long)g.M * g.N * g.K >= kTcMinWork && g.M >= 64 && g.K >= 8)
+      return gemm_tc(g, tc_mode(), 0, status, st);
     return gemm_f32(g, gemm_f32_pick(g), st);
   }
   static constexpr long long kTcMinWork = 1 << 15;
@@ -712,7 +777,7 @@ struct pepsvmc_ctx {
         ma.n = tb[m + 1] * a[m].Dr * bb[m + 1];
         ma.spins = spins; ma.spin_stride = (long long)Ly * Lx;
         ma.site_a = a[m].spin; ma.site_b = a[m + 1].spin;
-        ma.key = cfg.seed; ma.sweep = sweep_counter;
+        ma.key = cfg.seed; ma.sweep = d_sweep;
         ma.bond = bond_base + k * (Lxo - 1) + m;
         ma.out = l3[0]; ma.bs_out = S;
         ma.trace_ratio = trace_on ? trace_ratio : nullptr;
@@ -743,9 +808,80 @@ struct pepsvmc_ctx {
     PV_CUDA(top_down_all(1, st_bot));
     PV_CUDA(row_phase(0, st_top, false, st_bot, Lx * (Ly - 1)));
     top_valid = true;
-    ++sweep_counter;
     return cudaSuccess;
   }
+
+  // Publish the host's sweep counter to the device for the next sweep.
+  cudaError_t set_sweep() {
+    ++launches;
+    return k_set_u64(d_sweep, sweep_counter, st);
+  }
+
+  // ------------------------------------------------------ one sample step as a graph
+  // Sweep, fresh environments, E_loc, G and the float64 sums of every chain: the same
+  // launches every time (all per-chain choices are device data), so after one eager
+  // pass (which also runs the autotuner and builds the sketches) the whole sequence is
+  // captured once into a CUDA graph on the context's own non-blocking stream and
+  // replayed, ordered against the caller's stream by events.
+  bool use_graphs = true;
+  cudaStream_t gst = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  cudaEvent_t g_in = nullptr, g_out = nullptr;
+  int eager_steps = 0;
+
+  cudaError_t sample_step_body() {
+    PV_CUDA(sweep_once());
+    PV_CUDA(measure_dev());
+    launches += 2;
+    PV_CUDA(k_energy_accum(eloc, C, sums, st));
+    return k_grad_accum(G, Ph, Ph, elem_site, d_site_half_off, d_site_full_off, d_site_size, d_site_spin, spins,
+                        (long long)Ly * Lx, eloc, C, sumG, sumGE, st);
+  }
+  void drop_graph() {
+    if (step_exec) cudaGraphExecDestroy(step_exec);
+    step_exec = nullptr;
+  }
+  cudaError_t sample_step() {
+    PV_CUDA(set_sweep());
+    const bool graphable = use_graphs && !dry && !prof && !trace_on;
+    if (!graphable || eager_steps < 1) {
+      ++eager_steps;
+      return sample_step_body();
+    }
+    if (!gst) {
+      PV_CUDA(cudaStreamCreateWithFlags(&gst, cudaStreamNonBlocking));
+      PV_CUDA(cudaEventCreateWithFlags(&g_in, cudaEventDisableTiming));
+      PV_CUDA(cudaEventCreateWithFlags(&g_out, cudaEventDisableTiming));
+    }
+    PV_CUDA(cudaEventRecord(g_in, st));
+    PV_CUDA(cudaStreamWaitEvent(gst, g_in, 0));
+    if (!step_exec) {
+      cudaStream_t user = st;
+      st = gst;
+      capturing = true;
+      const long long l0 = launches;
+      cudaError_t e = cudaStreamBeginCapture(gst, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) e = sample_step_body();
+      cudaGraph_t graph = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(gst, &graph);
+      capturing = false;
+      st = user;
+      graph_launches = launches - l0;
+      launches = l0;
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&step_exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        drop_graph();
+        return e;
+      }
+    }
+    launches += graph_launches;
+    PV_CUDA(cudaGraphLaunch(step_exec, gst));
+    PV_CUDA(cudaEventRecord(g_out, gst));
+    return cudaStreamWaitEvent(st, g_out, 0);
+  }
+  long long graph_launches = 0;
 
   // ------------------------------------------------ measurement (Eqs. (3)-(7), App. C)
   cudaError_t measure_dev() {
@@ -1071,6 +1207,7 @@ int setup(pepsvmc_ctx* x, const double* tensors, const double* sketch) {
   ALLOC(x->exps, C);
   ALLOC(x->status, 1);
   ALLOC(x->counters, 2);
+  ALLOC(x->d_sweep, 1);
   // site tables for the gradient accumulation
   {
     std::vector<int> es(x->Ph), sp(Ly * Lx);
@@ -1151,6 +1288,10 @@ void pepsvmc_destroy(pepsvmc_ctx* x) {
     else cudaDeviceSynchronize();  // NOLINT
   }
   x->collect();
+  x->drop_graph();
+  if (x->gst) cudaStreamDestroy(x->gst);
+  if (x->g_in) cudaEventDestroy(x->g_in);
+  if (x->g_out) cudaEventDestroy(x->g_out);
   for (cudaEvent_t e : x->ev_pool) cudaEventDestroy(e);
   for (void* p : x->allocs) cudaFree(p);
   delete x;
@@ -1205,6 +1346,42 @@ int pepsvmc_get_profile_shapes(pepsvmc_ctx* x, char* buf, int64_t len) {
   }
   js += "]";
   if ((int64_t)js.size() + 1 > len) return x->fail(PEPSVMC_EINVAL, "profile text longer than the buffer");
+  memcpy(buf, js.c_str(), js.size() + 1);
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_set_graphs(pepsvmc_ctx* x, int32_t on) {
+  if (!x) return PEPSVMC_EINVAL;
+  x->use_graphs = on != 0;
+  x->drop_graph();
+  x->eager_steps = 0;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_set_autotune(pepsvmc_ctx* x, int32_t on) {
+  if (!x) return PEPSVMC_EINVAL;
+  x->autotune = on != 0;
+  if (!on) x->tuned.clear();
+  x->drop_graph();
+  x->eager_steps = 0;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_get_tuning(pepsvmc_ctx* x, char* buf, int64_t len) {
+  if (!x || !buf || len < 2) return PEPSVMC_EINVAL;
+  std::string js = "[";
+  for (const auto& kv : x->tuned) {
+    const int c = kv.second;
+    std::string times;
+    for (float t : x->tune_ms[kv.first]) times += (times.empty() ? "" : ",") + std::to_string(t);
+    char row[512];
+    snprintf(row, sizeof(row), "%s{\"shape\":\"%s\",\"choice\":\"%s%d\",\"candidate_ms\":[%s]}",
+             js.size() > 1 ? "," : "", kv.first.c_str(), c >= 100 ? "tc_bn" : "f32_cfg", c >= 100 ? c - 100 : c,
+             times.c_str());
+    js += row;
+  }
+  js += "]";
+  if ((int64_t)js.size() + 1 > len) return x->fail(PEPSVMC_EINVAL, "tuning text longer than the buffer");
   memcpy(buf, js.c_str(), js.size() + 1);
   return PEPSVMC_OK;
 }
@@ -1286,7 +1463,11 @@ int pepsvmc_get_trace(pepsvmc_ctx* x, double* ratio, int8_t* decision) {
 int pepsvmc_sample_sweep(pepsvmc_ctx* x, int32_t n, double* rate) {
   if (!x || n < 0) return PEPSVMC_EINVAL;
   cudaError_t e = x->ms(x->counters, 0, 2 * sizeof(unsigned long long));
-  for (int i = 0; i < n && e == cudaSuccess; ++i) e = x->sweep_once();
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    e = x->set_sweep();
+    if (e == cudaSuccess) e = x->sweep_once();
+    ++x->sweep_counter;
+  }
   if (e != cudaSuccess) return x->fail_cuda(e);
   int rc = x->check_status();
   if (rc) return rc;
@@ -1342,13 +1523,10 @@ int pepsvmc_energy_and_grad(pepsvmc_ctx* x, int32_t n, double* E_mean, double* E
       (e = x->ms(x->counters, 0, 2 * sizeof(unsigned long long))))
     return x->fail_cuda(e);
   for (int t = 0; t < n; ++t) {
-    if ((e = x->sweep_once()) || (e = x->measure_dev())) return x->fail_cuda(e);
-    x->launches += 2;
-    if ((e = k_energy_accum(x->eloc, x->C, x->sums, x->st))) return x->fail_cuda(e);
-    if ((e = k_grad_accum(x->G, x->Ph, x->Ph, x->elem_site, x->d_site_half_off, x->d_site_full_off, x->d_site_size,
-                          x->d_site_spin, x->spins, (long long)x->Ly * x->Lx, x->eloc, x->C, x->sumG, x->sumGE,
-                          x->st)))
-      return x->fail_cuda(e);
+    if ((e = x->sample_step())) return x->fail_cuda(e);
+    ++x->sweep_counter;
+    x->top_valid = true;
+    x->have_measure = true;
     if (eloc && (e = x->cp(eloc + (size_t)t * x->C, x->eloc, x->C * sizeof(double), cudaMemcpyDeviceToHost)))
       return x->fail_cuda(e);
     if (logpsi && (e = x->cp(logpsi + (size_t)t * x->C, x->logpsi, x->C * sizeof(double), cudaMemcpyDeviceToHost)))

@@ -55,6 +55,7 @@ __global__ void fill_kernel(float* p, long long n, float v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     p[i] = v;
 }
+__global__ void set_u64_kernel(unsigned long long* p, unsigned long long v) { *p = v; }
 __global__ void fill_d_kernel(double* p, long long n, double v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     p[i] = v;
@@ -152,7 +153,7 @@ __global__ void metropolis_kernel(const MetropolisArgs a) {
           atomicOr(a.status, ST_NONFINITE);
         } else {
           const uint4 w = philox4x32_10(
-              make_uint4((unsigned)b, (unsigned)a.sweep, (unsigned)a.bond, kTagMetropolis),
+              make_uint4((unsigned)b, (unsigned)*a.sweep, (unsigned)a.bond, kTagMetropolis),
               make_uint2((unsigned)(a.key & 0xffffffffull), (unsigned)(a.key >> 32)));
           const double u = uniform24(w.x);
           const double p = fmin(1.0, rho * rho);
@@ -330,6 +331,11 @@ bool g_dry_run = false;
 cudaError_t k_fill(float* p, long long n, float v, cudaStream_t st) {
   if (g_dry_run) return cudaSuccess;
   fill_kernel<<<grid_for(n), 256, 0, st>>>(p, n, v);
+  return cudaGetLastError();
+}
+cudaError_t k_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  set_u64_kernel<<<1, 1, 0, st>>>(p, v);
   return cudaGetLastError();
 }
 cudaError_t k_fill_d(double* p, long long n, double v, cudaStream_t st) {

@@ -16,7 +16,7 @@ struct MetropolisArgs {
   int8_t* spins; long long spin_stride;
   int site_a, site_b;                    // original lattice indices k*Lx+m of the pair
   unsigned long long key;                // Philox key (seed)
-  unsigned long long sweep;
+  const unsigned long long* sweep;       // device-resident sweep counter (read at run time)
   int bond;
   float* out; long long bs_out;          // selected, normalised L(m)
   double* trace_ratio; int8_t* trace_dec; long long trace_stride;  // nullable
@@ -25,6 +25,7 @@ struct MetropolisArgs {
 };
 
 cudaError_t k_fill(float* p, long long n, float v, cudaStream_t st);
+cudaError_t k_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
 cudaError_t k_fill_d(double* p, long long n, double v, cudaStream_t st);
 cudaError_t k_gather_f32(float* dst, const double* src, const int* map, long long n, cudaStream_t st);
 cudaError_t k_normalize_pow2(float* x, long long bs, int n, float* x2, long long bs2, int n2,
