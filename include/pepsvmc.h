@@ -187,6 +187,45 @@ int pepsvmc_env3_left_noalloc(const float* E, const float* T, const float* A,
                               int32_t cB2, int32_t Dl, int32_t Dr, int32_t Du, int32_t Dd,
                               void* stream);
 
+/* ------------------------------------------------------------- learned proposal
+ * Exact Metropolis-Hastings moves proposed by a small convolutional network (no
+ * counterpart in the paper's Sec. II sampler; it uses the MH form of Eq. (8) with a
+ * learned q).  Network: three 3x3 zero-padded convolutions on the +-1 grid, 1 -> 32 ->
+ * 32 -> 2 channels, ReLU after the first two; parameters (float64 on the host, 10146
+ * entries) in the order w1 (32,1,3,3), b1 (32), w2 (32,32,3,3), b2 (32), w3 (2,32,3,3),
+ * b3 (2).  Output channel 0 at (k,m) is the logit of bond (k,m)-(k,m+1), channel 1 of
+ * (k,m)-(k+1,m).  A learned sweep visits bands (k, k+1), k = 0..Ly-2: one or two
+ * site-disjoint antiparallel pairs of the band are drawn from softmaxes of their
+ * logits (two pairs with probability 1/2) and swapped; the move is accepted with
+ * min[1, |Psi'/Psi|^2 q(S|S')/q(S'|S)], Psi'/Psi from the band's four-line closure,
+ * Philox counter (chain, sweep, 4k+j, "LERN").
+ *   set/get_proposal_params: the network (float64 host array of 10146).
+ *   proposal_logits: logits of the current spins, host float64 [chain][2][Ly][Lx].
+ *   proposal_collect: n sweeps of the plain sampler, each followed by a measurement;
+ *     appends every chain's configuration and its measured NN amplitude ratios to a
+ *     device-resident training set.
+ *   proposal_train: Adam epochs (minibatches of `batch` configurations) on the mean
+ *     squared error between each antiparallel bond's logit and log min(1, rho^2)
+ *     (clipped at -20); loss_out (nullable) gets the last epoch's mean.
+ *   set_proposal: 0 = plain sequential sweeps only; 1 = every sample step of
+ *     pepsvmc_energy_and_grad adds one learned sweep after the plain sweep.
+ *   learned_sweep: n learned sweeps alone; accept_rate_out (nullable).
+ *   get_learned_trace: last learned sweep per [chain][band]: ratio Psi'/Psi,
+ *     ln q(S|S') - ln q(S'|S), decision (-1 nothing proposed, 0, 1); needs tracing on.
+ * Errors: ESTATE before set_proposal_params or with too small a training set.   */
+int pepsvmc_set_proposal_params(pepsvmc_ctx* ctx, const double* params);
+int pepsvmc_get_proposal_params(pepsvmc_ctx* ctx, double* params);
+int pepsvmc_proposal_logits(pepsvmc_ctx* ctx, double* out);
+int pepsvmc_proposal_collect(pepsvmc_ctx* ctx, int32_t n_sweeps);
+int64_t pepsvmc_proposal_dataset_size(const pepsvmc_ctx* ctx);
+/* Replace the training set by n host configurations (int8 [n][Ly][Lx]) and ratios
+ * (float64 [n][2][Ly][Lx], same channel layout as the logits).                   */
+int pepsvmc_proposal_load(pepsvmc_ctx* ctx, const int8_t* spins, const double* rho, int64_t n);
+int pepsvmc_proposal_train(pepsvmc_ctx* ctx, int32_t epochs, int32_t batch, double lr, double* loss_out);
+int pepsvmc_set_proposal(pepsvmc_ctx* ctx, int32_t mode);
+int pepsvmc_learned_sweep(pepsvmc_ctx* ctx, int32_t n_sweeps, double* accept_rate_out);
+int pepsvmc_get_learned_trace(pepsvmc_ctx* ctx, double* rho, double* dlq, int8_t* decision);
+
 /* Kernel launches issued by this context since its creation (a counter kept by
  * the host side of the library). */
 int64_t pepsvmc_launch_count(const pepsvmc_ctx* ctx);

@@ -46,6 +46,19 @@ def init_params(seed):
     return p
 
 
+def params_from_flat(flat):
+    """The network's parameter list from one flat array (w1, b1, w2, b2, w3, b3)."""
+    shapes = [(CHANNELS, 1, 3, 3), (CHANNELS,), (CHANNELS, CHANNELS, 3, 3), (CHANNELS,), (2, CHANNELS, 3, 3), (2,)]
+    out, off = [], 0
+    for s in shapes:
+        n = int(np.prod(s))
+        out.append(np.array(flat[off:off + n], dtype=np.float64).reshape(s))
+        off += n
+    if off != len(flat):
+        raise ValueError("wrong number of network parameters")
+    return out
+
+
 def conv3(x, w, b):
     """Zero-padded 3x3 convolution: x (B, Cin, Ly, Lx), w (Cout, Cin, 3, 3)."""
     B, Cin, Ly, Lx = x.shape

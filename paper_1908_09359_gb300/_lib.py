@@ -15,6 +15,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EZEROPSI, ESTATE = 0, -1, -2, -
 FP32, MIXED_BF16, MIXED_TF32, MIXED_BF16X3 = 0, 1, 2, 3
 
 NOALLOC_SCRATCH_FLOATS = 4194304  # PEPSVMC_NOALLOC_SCRATCH_FLOATS
+NET_PARAMS = 10146                # parameters of the proposal network
 
 ERRORS = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
           ENONFINITE: "ENONFINITE", EZEROPSI: "EZEROPSI", ESTATE: "ESTATE"}
@@ -28,7 +29,9 @@ SYMBOLS = [
     "pepsvmc_get_chain_grad", "pepsvmc_amplitude", "pepsvmc_energy_and_grad", "pepsvmc_update",
     "pepsvmc_launch_count", "pepsvmc_set_profiling", "pepsvmc_get_profile", "pepsvmc_env3_left",
     "pepsvmc_env3_left_noalloc", "pepsvmc_get_profile_shapes", "pepsvmc_set_autotune", "pepsvmc_get_tuning",
-    "pepsvmc_set_graphs",
+    "pepsvmc_set_graphs", "pepsvmc_set_proposal_params", "pepsvmc_get_proposal_params",
+    "pepsvmc_proposal_logits", "pepsvmc_proposal_collect", "pepsvmc_proposal_dataset_size", "pepsvmc_proposal_load",
+    "pepsvmc_proposal_train", "pepsvmc_set_proposal", "pepsvmc_learned_sweep", "pepsvmc_get_learned_trace",
 ]
 
 
@@ -88,6 +91,16 @@ def load(path: str | None = None):
         "pepsvmc_get_profile_shapes": (C.c_int, [P, C.c_char_p, I64]),
         "pepsvmc_set_autotune": (C.c_int, [P, I32]),
         "pepsvmc_set_graphs": (C.c_int, [P, I32]),
+        "pepsvmc_set_proposal_params": (C.c_int, [P, D]),
+        "pepsvmc_get_proposal_params": (C.c_int, [P, D]),
+        "pepsvmc_proposal_logits": (C.c_int, [P, D]),
+        "pepsvmc_proposal_collect": (C.c_int, [P, I32]),
+        "pepsvmc_proposal_dataset_size": (I64, [P]),
+        "pepsvmc_proposal_load": (C.c_int, [P, I8, D, I64]),
+        "pepsvmc_proposal_train": (C.c_int, [P, I32, I32, C.c_double, D]),
+        "pepsvmc_set_proposal": (C.c_int, [P, I32]),
+        "pepsvmc_learned_sweep": (C.c_int, [P, I32, D]),
+        "pepsvmc_get_learned_trace": (C.c_int, [P, D, D, I8]),
         "pepsvmc_get_tuning": (C.c_int, [P, C.c_char_p, I64]),
     }
     for name, (res, args) in sig.items():

@@ -182,6 +182,51 @@ class PepsVMC:
         self._check(self.lib.pepsvmc_get_profile_shapes(self.ctx, buf, len(buf)))
         return json.loads(buf.value.decode())
 
+    # ------------------------------------------------------------- learned proposal
+    def set_proposal_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        if p.size != _lib.NET_PARAMS:
+            raise ValueError(f"proposal network needs {_lib.NET_PARAMS} parameters")
+        self._check(self.lib.pepsvmc_set_proposal_params(self.ctx, _dp(p)))
+
+    def get_proposal_params(self):
+        p = np.empty(_lib.NET_PARAMS)
+        self._check(self.lib.pepsvmc_get_proposal_params(self.ctx, _dp(p)))
+        return p
+
+    def proposal_logits(self):
+        out = np.empty((self.n_chains, 2, self.Ly, self.Lx))
+        self._check(self.lib.pepsvmc_proposal_logits(self.ctx, _dp(out)))
+        return out
+
+    def proposal_collect(self, n_sweeps):
+        self._check(self.lib.pepsvmc_proposal_collect(self.ctx, int(n_sweeps)))
+        return int(self.lib.pepsvmc_proposal_dataset_size(self.ctx))
+
+    def proposal_load(self, spins, rho):
+        s = np.ascontiguousarray(spins, dtype=np.int8)
+        r = np.ascontiguousarray(rho, dtype=np.float64)
+        self._check(self.lib.pepsvmc_proposal_load(self.ctx, _i8(s), _dp(r), len(s)))
+
+    def proposal_train(self, epochs, batch, lr):
+        loss = C.c_double()
+        self._check(self.lib.pepsvmc_proposal_train(self.ctx, int(epochs), int(batch), float(lr), C.byref(loss)))
+        return loss.value
+
+    def set_proposal(self, mode):
+        self._check(self.lib.pepsvmc_set_proposal(self.ctx, int(mode)))
+
+    def learned_sweep(self, n=1):
+        r = C.c_double()
+        self._check(self.lib.pepsvmc_learned_sweep(self.ctx, int(n), C.byref(r)))
+        return r.value
+
+    def get_learned_trace(self):
+        shp = (self.n_chains, self.Ly - 1)
+        rho, dlq, dec = np.empty(shp), np.empty(shp), np.empty(shp, dtype=np.int8)
+        self._check(self.lib.pepsvmc_get_learned_trace(self.ctx, _dp(rho), _dp(dlq), _i8(dec)))
+        return rho, dlq, dec
+
     def set_graphs(self, on=True):
         self._check(self.lib.pepsvmc_set_graphs(self.ctx, 1 if on else 0))
 

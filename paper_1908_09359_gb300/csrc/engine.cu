@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "pepsvmc.h"
+#include "proposal.cuh"
 #include "stages.cuh"
 
 using namespace pv;
@@ -407,13 +408,17 @@ struct pepsvmc_ctx {
     return k_dot(a, bsa, b, bsb, n, out, C, status, st);
   }
 
+  // rho_export (nullable): [chain][2][Ly][Lx] receives each NN ratio at (channel, site).
+  float* rho_export = nullptr;
   cudaError_t ratio(const float* a, long long bsa, const float* b, long long bsb, int n, int si, int sj,
-                    double halfJ) {
+                    double halfJ, long long export_idx = -1) {
     if (!chains(a, bsa, n, 4, "ratio a") || !chains(b, bsb, n, 4, "ratio b") ||
         !chains(spins, (long long)Ly * Lx, (long long)std::max(si, sj) + 1, 1, "ratio spins"))
       return cudaErrorInvalidValue;
     ++launches;
-    return k_ratio_accum(a, bsa, b, bsb, n, den, spins, (long long)Ly * Lx, si, sj, halfJ, eloc, C, status, st);
+    float* ro = (rho_export && export_idx >= 0) ? rho_export : nullptr;
+    return k_ratio_accum(a, bsa, b, bsb, n, den, spins, (long long)Ly * Lx, si, sj, halfJ, eloc, C, status, st, ro,
+                         2LL * Ly * Lx, export_idx);
   }
 
   cudaError_t logpsi_of(const float* x, long long bs, const double* logT, const double* logB) {
@@ -423,11 +428,12 @@ struct pepsvmc_ctx {
     return k_logpsi(x, bs, exps, logT, logB, logpsi, sign, C, status, st);
   }
 
+  const int8_t* sel_base = nullptr;  // spin array the site tensors are selected from (default: spins)
   void sel(GemmDesc& g, const SiteOp& a, const float* base, int flip) const {
     g.B = base;
     g.ssB = a.size;
     g.bsB = 0;
-    g.sel = spins + a.spin;
+    g.sel = (sel_base ? sel_base : spins) + a.spin;
     g.sel_stride = (long long)Ly * Lx;
     g.sel_xor = flip;
   }
@@ -831,6 +837,7 @@ struct pepsvmc_ctx {
 
   cudaError_t sample_step_body() {
     PV_CUDA(sweep_once());
+    if (proposal_mode == 1) PV_CUDA(learned_sweep());
     PV_CUDA(measure_dev());
     launches += 2;
     PV_CUDA(k_energy_accum(eloc, C, sums, st));
@@ -928,7 +935,7 @@ struct pepsvmc_ctx {
         if (!edge) {
           PV_CUDA(left3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], 1, B.site(m),
                         B.chain_stride, bb[m + 1], fl, S));
-          PV_CUDA(ratio(fl, S, envRfp(m + 1), S, n, a[m].spin, a[m + 1].spin, 0.5 * cfg.J1));
+          PV_CUDA(ratio(fl, S, envRfp(m + 1), S, n, a[m].spin, a[m + 1].spin, 0.5 * cfg.J1, (long long)k * Lx + m));
         }
         PV_CUDA(delta3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], B.site(m),
                        B.chain_stride, bb[m + 1], Rin, bsR, den, G + site_half_off[(size_t)k * Lx + m], Ph));
@@ -980,7 +987,7 @@ struct pepsvmc_ctx {
       PV_CUDA(step(Lin, bsL, 0, 0, cur));
       PV_CUDA(dot(cur, S4, Rin, bsR, n, den));
       PV_CUDA(step(Lin, bsL, 1, 1, fl4));
-      PV_CUDA(ratio(fl4, S4, Rin, bsR, n, a1[m].spin, a2[m].spin, 0.5 * cfg.J1));
+      PV_CUDA(ratio(fl4, S4, Rin, bsR, n, a1[m].spin, a2[m].spin, 0.5 * cfg.J1, (long long)Ly * Lx + k * Lx + m));
       float *Ptn = nullptr, *Pbn = nullptr;
       if (cfg.J2 != 0.0) {
         if (m >= 1) {
@@ -1002,6 +1009,139 @@ struct pepsvmc_ctx {
       Pt = Ptn;
       Pb = Pbn;
     }
+    return cudaSuccess;
+  }
+
+  // ------------------------------------------------------------ learned proposal
+  // One exact MH move per row band (k, k+1), bands top-down k = 0..Ly-2; T_k is
+  // rebuilt after the band above it moved, B_{k+1} comes from the start of the sweep.
+  int proposal_mode = 0;
+  bool net_ready = false;
+  float *net = nullptr, *net_g = nullptr, *net_m = nullptr, *net_v = nullptr;
+  float *h1 = nullptr, *h2 = nullptr, *logits = nullptr, *logits2 = nullptr;
+  int8_t* prop = nullptr;
+  int* move = nullptr;
+  double *lq_fwd = nullptr, *lq_rev = nullptr, *net_acc = nullptr;
+  int *ex_den = nullptr, *ex_num = nullptr;
+  unsigned long long* lcount = nullptr;
+  double *ltr_rho = nullptr, *ltr_dlq = nullptr;
+  int8_t* ltr_dec = nullptr;
+  int adam_t = 0;
+  // training set collected from the plain sampler: spins and the measured NN ratios
+  int8_t* ds_spins = nullptr;
+  float* ds_rho = nullptr;
+  long long ds_cap = 0, ds_n = 0;
+  float *tr_h1 = nullptr, *tr_h2 = nullptr, *tr_out = nullptr, *tr_d1 = nullptr, *tr_d2 = nullptr;
+  int tr_batch = 0;
+
+  cudaError_t net_alloc() {
+    if (net) return cudaSuccess;
+    const long long N = (long long)Ly * Lx;
+    PV_CUDA(alloc(&net, kNetParams));
+    PV_CUDA(alloc(&net_g, kNetParams));
+    PV_CUDA(alloc(&net_m, kNetParams));
+    PV_CUDA(alloc(&net_v, kNetParams));
+    PV_CUDA(alloc(&h1, (size_t)C * kNetC * N));
+    PV_CUDA(alloc(&h2, (size_t)C * kNetC * N));
+    PV_CUDA(alloc(&logits, (size_t)C * 2 * N));
+    PV_CUDA(alloc(&logits2, (size_t)C * 2 * N));
+    PV_CUDA(alloc(&prop, (size_t)C * N));
+    PV_CUDA(alloc(&move, (size_t)C * 4));
+    PV_CUDA(alloc(&lq_fwd, C));
+    PV_CUDA(alloc(&lq_rev, C));
+    PV_CUDA(alloc(&net_acc, 2));
+    PV_CUDA(alloc(&ex_den, C));
+    PV_CUDA(alloc(&ex_num, C));
+    PV_CUDA(alloc(&lcount, 2));
+    PV_CUDA(alloc(&ltr_rho, (size_t)C * (Ly - 1)));
+    PV_CUDA(alloc(&ltr_dlq, (size_t)C * (Ly - 1)));
+    PV_CUDA(alloc(&ltr_dec, (size_t)C * (Ly - 1)));
+    PV_CUDA(ms(net_m, 0, kNetParams * sizeof(float)));
+    PV_CUDA(ms(net_v, 0, kNetParams * sizeof(float)));
+    PV_CUDA(ms(lcount, 0, 2 * sizeof(unsigned long long)));
+    return cudaSuccess;
+  }
+
+  // Four-line closure of band k for spin array sp: out points at the final scalar.
+  cudaError_t band_closure(int k, const View& T, const View& B, const int8_t* sp, float* ba, float* bb, int* ex,
+                           float** out) {
+    const std::vector<int>& tb = *T.bond;
+    const std::vector<int>& bbd = *B.bond;
+    PV_CUDA(ms(ex, 0, C * sizeof(int)));
+    sel_base = sp;
+    const float* Lin = ones;
+    long long bsL = 1;
+    float* cur = ba;
+    for (int m = 0; m < Lx; ++m) {
+      const SiteOp a1 = site(0, k, m), a2 = site(0, k + 1, m);
+      cur = (m % 2 == 0) ? ba : bb;
+      cudaError_t e = left4(Lin, bsL, tb[m], bbd[m], T.site(m), T.chain_stride, tb[m + 1], a1, 0, a2, 0, B.site(m),
+                            B.chain_stride, bbd[m + 1], cur, S4);
+      if (e == cudaSuccess && m + 1 < Lx)
+        e = norm2(cur, S4, tb[m + 1] * a1.Dr * a2.Dr * bbd[m + 1], nullptr, 0, nullptr, 0, ex);
+      if (e != cudaSuccess) {
+        sel_base = nullptr;
+        return e;
+      }
+      Lin = cur;
+      bsL = S4;
+    }
+    sel_base = nullptr;
+    *out = cur;
+    return cudaSuccess;
+  }
+
+  cudaError_t learned_sweep() {
+    PV_CUDA(top_down_all(1, st_bot));
+    const long long N = (long long)Ly * Lx;
+    const NetParams w = NetParams::at(net);
+    for (int k = 0; k + 1 < Ly; ++k) {
+      const View T = view(st_top, k, k);
+      const View B = view(st_bot, Ly - 2 - k, Ly - 2 - k);
+      launches += 8;
+      PV_CUDA(net_forward(w, spins, C, Ly, Lx, h1, h2, logits, st));
+      PV_CUDA(propose_moves(logits, spins, prop, C, Ly, Lx, k, cfg.seed, d_sweep, move, lq_fwd, st));
+      PV_CUDA(net_forward(w, prop, C, Ly, Lx, h1, h2, logits2, st));
+      PV_CUDA(reverse_logq(logits2, prop, C, Ly, Lx, k, move, lq_rev, st));
+      float *den_p = nullptr, *num_p = nullptr;
+      PV_CUDA(band_closure(k, T, B, spins, l4[0], l4[1], ex_den, &den_p));
+      PV_CUDA(band_closure(k, T, B, prop, fl4, ptop[0], ex_num, &num_p));
+      ++launches;
+      PV_CUDA(accept_moves(spins, prop, C, (int)N, move, den_p, num_p, S4, ex_den, ex_num, lq_fwd, lq_rev, cfg.seed,
+                           d_sweep, k, Ly - 1, trace_on ? ltr_rho : nullptr, ltr_dlq, trace_on ? ltr_dec : nullptr,
+                           lcount, status, st));
+      PV_CUDA(compress(0, k, T, st_top, k + 1, k + 1));
+    }
+    top_valid = true;
+    return cudaSuccess;
+  }
+
+  cudaError_t train_epochs(int epochs, int batch, float lr, double* loss) {
+    const long long N = (long long)Ly * Lx;
+    if (batch != tr_batch) {
+      PV_CUDA(alloc(&tr_h1, (size_t)batch * kNetC * N));
+      PV_CUDA(alloc(&tr_h2, (size_t)batch * kNetC * N));
+      PV_CUDA(alloc(&tr_d1, (size_t)batch * kNetC * N));
+      PV_CUDA(alloc(&tr_d2, (size_t)batch * kNetC * N));
+      PV_CUDA(alloc(&tr_out, (size_t)batch * 2 * N));
+      tr_batch = batch;
+    }
+    const NetParams w = NetParams::at(net), g = NetParams::at(net_g);
+    double sse = 0.0, cnt = 0.0;
+    for (int ep = 0; ep < epochs; ++ep) {
+      sse = cnt = 0.0;
+      for (long long off = 0; off + batch <= ds_n; off += batch) {
+        ++adam_t;
+        launches += 12;
+        PV_CUDA(net_train_step(w, g, net_m, net_v, kNetParams, adam_t, lr, ds_spins + off * N, ds_rho + off * 2 * N,
+                               batch, Ly, Lx, tr_h1, tr_h2, tr_out, tr_d2, tr_d1, net_acc, st));
+        double a[2] = {0, 0};
+        PV_CUDA(cps(a, net_acc, sizeof(a), cudaMemcpyDeviceToHost));
+        sse += a[0];
+        cnt += a[1];
+      }
+    }
+    if (loss) *loss = cnt > 0 ? sse / cnt : 0.0;
     return cudaSuccess;
   }
 
@@ -1348,6 +1488,140 @@ int pepsvmc_get_profile_shapes(pepsvmc_ctx* x, char* buf, int64_t len) {
   if ((int64_t)js.size() + 1 > len) return x->fail(PEPSVMC_EINVAL, "profile text longer than the buffer");
   memcpy(buf, js.c_str(), js.size() + 1);
   return PEPSVMC_OK;
+}
+
+int pepsvmc_set_proposal_params(pepsvmc_ctx* x, const double* params) {
+  if (!x || !params) return PEPSVMC_EINVAL;
+  cudaError_t e = x->net_alloc();
+  if (e != cudaSuccess) return x->fail(PEPSVMC_ENOMEM, "proposal network allocation failed");
+  std::vector<float> h(params, params + kNetParams);
+  if ((e = x->cps(x->net, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice))) return x->fail_cuda(e);
+  x->net_ready = true;
+  x->drop_graph();
+  x->eager_steps = 0;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_get_proposal_params(pepsvmc_ctx* x, double* out) {
+  if (!x || !out) return PEPSVMC_EINVAL;
+  if (!x->net_ready) return x->fail(PEPSVMC_ESTATE, "no proposal network: call pepsvmc_set_proposal_params");
+  std::vector<float> h(kNetParams);
+  cudaError_t e = x->cps(h.data(), x->net, h.size() * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  for (int i = 0; i < kNetParams; ++i) out[i] = h[i];
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_proposal_logits(pepsvmc_ctx* x, double* out) {
+  if (!x || !out) return PEPSVMC_EINVAL;
+  if (!x->net_ready) return x->fail(PEPSVMC_ESTATE, "no proposal network: call pepsvmc_set_proposal_params");
+  const long long n = (long long)x->C * 2 * x->Ly * x->Lx;
+  cudaError_t e = net_forward(NetParams::at(x->net), x->spins, x->C, x->Ly, x->Lx, x->h1, x->h2, x->logits, x->st);
+  std::vector<float> h(n);
+  if (e == cudaSuccess) e = x->cps(h.data(), x->logits, n * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  for (long long i = 0; i < n; ++i) out[i] = h[i];
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_proposal_collect(pepsvmc_ctx* x, int32_t n_sweeps) {
+  if (!x || n_sweeps < 1) return PEPSVMC_EINVAL;
+  const long long N = (long long)x->Ly * x->Lx, need = x->ds_n + (long long)n_sweeps * x->C;
+  cudaError_t e = cudaSuccess;
+  if (need > x->ds_cap) {
+    int8_t* s2 = nullptr;
+    float* r2 = nullptr;
+    if ((e = x->alloc(&s2, (size_t)need * N)) || (e = x->alloc(&r2, (size_t)need * 2 * N)))
+      return x->fail(PEPSVMC_ENOMEM, "training set allocation failed");
+    if (x->ds_n && ((e = x->cp(s2, x->ds_spins, x->ds_n * N, cudaMemcpyDeviceToDevice)) ||
+                    (e = x->cp(r2, x->ds_rho, x->ds_n * 2 * N * sizeof(float), cudaMemcpyDeviceToDevice))))
+      return x->fail_cuda(e);
+    x->ds_spins = s2;
+    x->ds_rho = r2;
+    x->ds_cap = need;
+  }
+  for (int t = 0; t < n_sweeps; ++t) {
+    if ((e = x->set_sweep()) || (e = x->sweep_once())) return x->fail_cuda(e);
+    x->rho_export = x->ds_rho + x->ds_n * 2 * N;
+    e = x->measure_dev();
+    x->rho_export = nullptr;
+    if (e || (e = x->cp(x->ds_spins + x->ds_n * N, x->spins, (size_t)x->C * N, cudaMemcpyDeviceToDevice)))
+      return x->fail_cuda(e);
+    x->ds_n += x->C;
+    ++x->sweep_counter;
+  }
+  return x->check_status();
+}
+
+int64_t pepsvmc_proposal_dataset_size(const pepsvmc_ctx* x) { return x ? x->ds_n : 0; }
+
+int pepsvmc_proposal_load(pepsvmc_ctx* x, const int8_t* spins, const double* rho, int64_t n) {
+  if (!x || !spins || !rho || n < 1) return PEPSVMC_EINVAL;
+  const long long N = (long long)x->Ly * x->Lx;
+  cudaError_t e;
+  if (n > x->ds_cap) {
+    if ((e = x->alloc(&x->ds_spins, (size_t)n * N)) || (e = x->alloc(&x->ds_rho, (size_t)n * 2 * N)))
+      return x->fail(PEPSVMC_ENOMEM, "training set allocation failed");
+    x->ds_cap = n;
+  }
+  std::vector<float> r(rho, rho + n * 2 * N);
+  if ((e = x->cps(x->ds_spins, spins, (size_t)n * N, cudaMemcpyHostToDevice)) ||
+      (e = x->cps(x->ds_rho, r.data(), r.size() * sizeof(float), cudaMemcpyHostToDevice)))
+    return x->fail_cuda(e);
+  x->ds_n = n;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_proposal_train(pepsvmc_ctx* x, int32_t epochs, int32_t batch, double lr, double* loss_out) {
+  if (!x || epochs < 1 || batch < 1) return PEPSVMC_EINVAL;
+  if (!x->net_ready) return x->fail(PEPSVMC_ESTATE, "no proposal network: call pepsvmc_set_proposal_params");
+  if (x->ds_n < batch) return x->fail(PEPSVMC_ESTATE, "training set smaller than one batch");
+  cudaError_t e = x->train_epochs(epochs, batch, (float)lr, loss_out);
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  x->drop_graph();
+  x->eager_steps = 0;
+  return x->check_status();
+}
+
+int pepsvmc_set_proposal(pepsvmc_ctx* x, int32_t mode) {
+  if (!x || mode < 0 || mode > 1) return PEPSVMC_EINVAL;
+  if (mode == 1 && !x->net_ready) return x->fail(PEPSVMC_ESTATE, "no proposal network: call pepsvmc_set_proposal_params");
+  x->proposal_mode = mode;
+  x->drop_graph();
+  x->eager_steps = 0;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_learned_sweep(pepsvmc_ctx* x, int32_t n, double* rate) {
+  if (!x || n < 0) return PEPSVMC_EINVAL;
+  if (!x->net_ready) return x->fail(PEPSVMC_ESTATE, "no proposal network: call pepsvmc_set_proposal_params");
+  cudaError_t e = x->ms(x->lcount, 0, 2 * sizeof(unsigned long long));
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    e = x->set_sweep();
+    if (e == cudaSuccess) e = x->learned_sweep();
+    ++x->sweep_counter;
+  }
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  int rc = x->check_status();
+  if (rc) return rc;
+  if (rate) {
+    unsigned long long h[2] = {0, 0};
+    if ((e = x->cps(h, x->lcount, sizeof(h), cudaMemcpyDeviceToHost))) return x->fail_cuda(e);
+    *rate = h[0] ? (double)h[1] / (double)h[0] : 0.0;
+  }
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_get_learned_trace(pepsvmc_ctx* x, double* rho, double* dlq, int8_t* dec) {
+  if (!x) return PEPSVMC_EINVAL;
+  if (!x->net || !x->trace_on) return x->fail(PEPSVMC_ESTATE, "learned trace needs a network and tracing on");
+  const size_t n = (size_t)x->C * (x->Ly - 1);
+  cudaError_t e = cudaSuccess;
+  if (rho) e = x->cp(rho, x->ltr_rho, n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && dlq) e = x->cp(dlq, x->ltr_dlq, n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && dec) e = x->cp(dec, x->ltr_dec, n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = x->sync();
+  return e == cudaSuccess ? PEPSVMC_OK : x->fail_cuda(e);
 }
 
 int pepsvmc_set_graphs(pepsvmc_ctx* x, int32_t on) {

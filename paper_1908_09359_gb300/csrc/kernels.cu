@@ -207,7 +207,8 @@ __global__ void dot_kernel(const float* a, long long bsa, const float* bb, long 
 
 __global__ void ratio_accum_kernel(const float* a, long long bsa, const float* bb, long long bsb, int n,
                                    const double* den, const int8_t* spins, long long spin_stride, int si, int sj,
-                                   double halfJ, double* eloc, unsigned* status) {
+                                   double halfJ, double* eloc, unsigned* status, float* rho_out, long long rho_stride,
+                                   long long rho_idx) {
   __shared__ double red[kThreads / 32];
   const int b = blockIdx.x;
   const int8_t* sp = spins + b * spin_stride;
@@ -221,6 +222,7 @@ __global__ void ratio_accum_kernel(const float* a, long long bsa, const float* b
     const double r = s / den[b];
     if (!isfinite(r)) atomicOr(status, ST_NONFINITE);
     eloc[b] += halfJ * r;
+    if (rho_out) rho_out[b * rho_stride + rho_idx] = (float)r;
   }
 }
 
@@ -373,10 +375,11 @@ cudaError_t k_dot(const float* a, long long bsa, const float* b, long long bsb, 
 }
 cudaError_t k_ratio_accum(const float* a, long long bsa, const float* b, long long bsb, int n, const double* den,
                           const int8_t* spins, long long spin_stride, int si, int sj, double halfJ, double* eloc,
-                          int batch, unsigned* status, cudaStream_t st) {
+                          int batch, unsigned* status, cudaStream_t st, float* rho_out, long long rho_stride,
+                          long long rho_idx) {
   if (g_dry_run) return cudaSuccess;
   ratio_accum_kernel<<<batch, kThreads, 0, st>>>(a, bsa, b, bsb, n, den, spins, spin_stride, si, sj, halfJ, eloc,
-                                                 status);
+                                                 status, rho_out, rho_stride, rho_idx);
   return cudaGetLastError();
 }
 cudaError_t k_eloc_diag(const int8_t* spins, int Ly, int Lx, double J1, double J2, double* eloc, int batch,

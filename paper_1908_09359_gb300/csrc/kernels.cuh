@@ -36,9 +36,11 @@ cudaError_t k_mps_normalize(float* x, long long bs, int n, const int* exps, cons
 cudaError_t k_metropolis(const MetropolisArgs& a, int batch, cudaStream_t st);
 cudaError_t k_dot(const float* a, long long bsa, const float* b, long long bsb, int n, double* out,
                   int batch, unsigned* status, cudaStream_t st);
+// rho_out (nullable): the ratio of chain c is also written to rho_out[c * rho_stride + rho_idx].
 cudaError_t k_ratio_accum(const float* a, long long bsa, const float* b, long long bsb, int n,
                           const double* den, const int8_t* spins, long long spin_stride, int si, int sj,
-                          double halfJ, double* eloc, int batch, unsigned* status, cudaStream_t st);
+                          double halfJ, double* eloc, int batch, unsigned* status, cudaStream_t st,
+                          float* rho_out = nullptr, long long rho_stride = 0, long long rho_idx = 0);
 cudaError_t k_eloc_diag(const int8_t* spins, int Ly, int Lx, double J1, double J2, double* eloc,
                         int batch, cudaStream_t st);
 cudaError_t k_logpsi(const float* x, long long bs, const int* exps, const double* logT,

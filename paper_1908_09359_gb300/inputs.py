@@ -105,6 +105,19 @@ def start_spins(n_chains: int, Ly: int, Lx: int, seed: int, kind: str = "random"
     return out.reshape(n_chains, Ly, Lx)
 
 
+def proposal_params(seed: int) -> np.ndarray:
+    """Initial weights of the proposal network as one float64 array in the order
+    w1 (32,1,3,3), b1 (32), w2 (32,32,3,3), b2 (32), w3 (2,32,3,3), b3 (2): Gaussian
+    entries scaled by sqrt(2 / fan-in) (He initialisation), the last layer by a further
+    0.1, zero biases."""
+    rng = np.random.default_rng(seed ^ 0xC0DE)
+    parts = []
+    for shape, extra in (((32, 1, 3, 3), 1.0), ((32, 32, 3, 3), 1.0), ((2, 32, 3, 3), 0.1)):
+        parts.append(rng.standard_normal(shape).ravel() * np.sqrt(2.0 / (shape[1] * 9)) * extra)
+        parts.append(np.zeros(shape[0]))
+    return np.concatenate(parts)
+
+
 def workload(name: str, n_chains: int | None = None) -> dict:
     """Everything a run of workload ``name`` needs, as plain arrays and numbers."""
     w = dict(WORKLOADS[name])

@@ -1,0 +1,130 @@
+"""The learned proposal on the GPU against the oracle (oracle/proposal.py).
+
+* network forward: logits within 1e-5 of the largest |logit| (FP32 direct convolution
+  vs float64);
+* one training step: loss within 1e-5 relative; parameters after one Adam step within
+  1e-6 + 1e-3 lr of the oracle's where the oracle gradient is not negligible (Adam's
+  first step is lr * g / |g|, so near-zero gradients may flip);
+* learned sweep: the same moves, ratios within 1e-5, log q differences within 1e-5,
+  identical decisions and final spins (tensors with simple-update-like bond spectra,
+  8x8 shapes, Dc = 16);
+* training on the plain sampler's configurations lowers the loss.
+"""
+import numpy as np
+import pytest
+
+from oracle import proposal, vmc
+from paper_1908_09359_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1908_09359_gb300 import api as a
+    from paper_1908_09359_gb300 import build
+    build.build()
+    return a
+
+
+def structured_8x8(n):
+    w = inputs.workload("peps_8x8", n_chains=n)
+    w["tensors"] = inputs.peps_tensors(8, 8, 4, w["seed"], True, bond_decay=1.0)
+    return w
+
+
+def test_network_forward_matches_oracle(api):
+    w = structured_8x8(6)
+    sp = inputs.start_spins(6, 8, 8, 3, "random")
+    flat = inputs.proposal_params(7)
+    ctx = api.PepsVMC(8, 8, 4, 16, 6, w["tensors"], w["sketch"], seed=1)
+    ctx.set_spins(sp)
+    ctx.set_proposal_params(flat)
+    got = ctx.proposal_logits()
+    ref = proposal.forward(proposal.params_from_flat(flat), sp)[0]
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+    ctx.close()
+
+
+def test_one_training_step_matches_oracle(api):
+    n = 32
+    rng = np.random.default_rng(5)
+    sp = inputs.start_spins(n, 8, 8, 8, "random")
+    rho = np.exp(rng.standard_normal((n, 2, 8, 8)))
+    flat = inputs.proposal_params(9)
+    w = structured_8x8(n)
+    ctx = api.PepsVMC(8, 8, 4, 16, n, w["tensors"], w["sketch"], seed=1)
+    ctx.set_proposal_params(flat)
+    ctx.proposal_load(sp, rho)
+    lr = 1e-3
+    loss = ctx.proposal_train(1, n, lr)
+    after = ctx.get_proposal_params()
+    params = proposal.params_from_flat(flat)
+    tgt, mask = proposal.bond_targets(sp, rho[:, 0, :, :-1], rho[:, 1, :-1, :])
+    ref_loss, grads = proposal.loss_and_grad(params, sp, tgt, mask)
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    state = ([np.zeros_like(p) for p in params], [np.zeros_like(p) for p in params])
+    ref_after = np.concatenate([p.ravel() for p in proposal.adam_step(params, grads, state, lr, 1)])
+    g = np.concatenate([x.ravel() for x in grads])
+    big = np.abs(g) > 1e-3 * np.max(np.abs(g))
+    assert np.max(np.abs(after - ref_after)[big]) <= 1e-6 + 1e-3 * lr
+    ctx.close()
+
+
+def test_learned_sweep_matches_oracle(api):
+    n = 4
+    w = structured_8x8(n)
+    g = vmc.unpack(w["tensors"], 8, 8, 4)
+    # start from configurations the oracle's own sampler reached (at uniformly random ones
+    # Psi(S) is often small and ratios of O(100) carry float32 errors above 1e-5)
+    sp = inputs.start_spins(n, 8, 8, 12, "random")
+    for c in range(n):
+        for t0 in range(3):
+            sp[c], _, _ = vmc.sweep(g, sp[c], 16, w["sketch"], 3, 99, c, t0)
+    flat = inputs.proposal_params(3)
+    seed, t = 17, 6
+    ctx = api.PepsVMC(8, 8, 4, 16, n, w["tensors"], w["sketch"], seed=seed)
+    ctx.set_spins(sp)
+    ctx.set_proposal_params(flat)
+    ctx.set_sweep_counter(t)
+    ctx.enable_trace(True)
+    # the learned sweep needs top environments of the current configuration
+    ctx.amplitude(0)
+    ctx.learned_sweep(1)
+    rho, dlq, dec = ctx.get_learned_trace()
+    final = ctx.get_spins()
+    params = proposal.params_from_flat(flat)
+    moved = 0
+    for c in range(n):
+        tr = []
+        new = proposal.learned_sweep(g, sp[c], 16, w["sketch"], 3, params, seed, c, t, trace=tr)
+        for k, move, r, d, acc in tr:
+            if move is None:
+                assert dec[c, k] == -1
+                continue
+            moved += 1
+            assert rho[c, k] == pytest.approx(r, rel=1e-5, abs=1e-5)
+            assert dlq[c, k] == pytest.approx(d, abs=1e-5)
+            assert int(dec[c, k]) == int(acc), (c, k)
+        assert np.array_equal(new, final[c])
+        assert int(final[c].sum()) == int(sp[c].sum())
+    assert moved > 10
+    ctx.close()
+
+
+def test_training_on_sampled_configurations_lowers_the_loss(api):
+    w = structured_8x8(256)
+    ctx = api.PepsVMC(8, 8, 4, 16, 256, w["tensors"], w["sketch"], seed=2)
+    ctx.set_spins(inputs.start_spins(256, 8, 8, 4, "random"))
+    ctx.set_proposal_params(inputs.proposal_params(1))
+    assert ctx.proposal_collect(4) == 1024
+    first = ctx.proposal_train(1, 64, 2e-3)
+    last = ctx.proposal_train(15, 64, 2e-3)
+    assert last < 0.7 * first, (first, last)
+    ctx.set_proposal(1)
+    r = ctx.energy_and_grad(2)
+    assert np.all(np.isfinite(r["eloc"]))
+    ctx.close()

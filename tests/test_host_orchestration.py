@@ -37,6 +37,12 @@ c.energy_and_grad(1)
 c.update(0.01, 1)
 c.enable_trace(True)
 c.sample_sweep(1)
+c.set_proposal_params(inputs.proposal_params(1))
+c.learned_sweep(1)
+c.proposal_collect(1)
+c.proposal_train(1, min(w["n_chains"], 64), 1e-3)
+c.set_proposal(1)
+c.energy_and_grad(2)
 print(json.dumps(dict(sweep=n1 - n0, measure=n2 - n1)))
 """
 
