@@ -41,7 +41,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="peps_24x24")
     p.add_argument("--n-fit", type=int, default=3)
-    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "tf32", "bf16x3"])
+    p.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "tf32", "bf16x3"],
+                   help="bf16x3 (split-BF16 tensor cores, the chosen form) or fp32 (plain)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -277,35 +278,53 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return
-    achieved = prof["gemm_flops"] / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else None
     step_ms = ms / args.steps
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm, hbm_src = peaks.get("hbm_gbs"), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    if hbm is None:
+        hbm, hbm_src = 6800.0, "fallback 6.8 TB/s (of fallback)"
     if args.precision == "fp32":
-        kname, bound, peak = "gemm_f32_kernel (batched contraction, FP32 CUDA cores)", "alu", FP32_ALU_PEAK_TFLOPS
-        psrc = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"
+        kname = "gemm_f32_kernel (batched contraction, FP32 CUDA cores)"
+        cbound, cpeak = "alu", FP32_ALU_PEAK_TFLOPS
+        csrc = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"
     else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         bf16 = peaks.get("bf16_tflops_sustained")
         src = "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
         if bf16 is None:
             bf16, src = 1700.0, "fallback sustained bf16 1.7 PFLOP/s (of fallback)"
-        # TF32 dense rate is half the BF16 rate (nominal 1.1 vs 2.25 PFLOP/s)
         # TF32 dense rate is half the BF16 rate; split BF16 issues three BF16 MMAs per
         # product, so its algorithmic flops are reported against a third of the BF16 peak
-        peak = {"bf16": bf16, "tf32": bf16 / 2.0, "bf16x3": bf16 / 3.0}[args.precision]
+        cpeak = {"bf16": bf16, "tf32": bf16 / 2.0, "bf16x3": bf16 / 3.0}[args.precision]
         kname = ("gemm_tc_kernel (batched contraction, tcgen05 "
                  + {"bf16": "kind::f16", "tf32": "kind::tf32", "bf16x3": "kind::f16, split hi+lo, 3 MMAs"}[
-                     args.precision] + ")")
-        bound = "tensor"
-        psrc = src + {"bf16": "", "tf32": " x 1/2 for TF32", "bf16x3": " x 1/3 for three BF16 MMAs"}[args.precision]
+                     args.precision] + ", tile autotuned per shape)")
+        cbound = "tensor"
+        csrc = src + {"bf16": "", "tf32": " x 1/2 for TF32", "bf16x3": " x 1/3 for three BF16 MMAs"}[args.precision]
+    flops, nbytes, gsec = prof["gemm_flops"], prof["gemm_bytes"], prof["gemm_ms"] / 1e3
+    intensity = flops / nbytes if nbytes > 0 else None
+    ridge = cpeak * 1e12 / (hbm * 1e9)
+    compute = {"bound": cbound, "achieved": flops / gsec / 1e12 if gsec > 0 else None, "peak": cpeak,
+               "unit": "TFLOP/s", "peak_source": csrc}
+    compute["frac"] = compute["achieved"] / cpeak if compute["achieved"] else None
+    memory = {"bound": "hbm", "achieved": nbytes / gsec / 1e9 if gsec > 0 else None, "peak": hbm,
+              "unit": "GB/s", "peak_source": hbm_src}
+    memory["frac"] = memory["achieved"] / hbm if memory["achieved"] else None
+    # The binding roofline: HBM when the contractions' algorithmic intensity lies below
+    # the ridge point of the compute peak, the compute unit otherwise.
+    bind, other = (memory, compute) if intensity is not None and intensity < ridge else (compute, memory)
     roofline = {
-        "kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-        "frac": achieved / peak if achieved else None, "peak_source": psrc,
+        "kernel": kname, "bound": bind["bound"], "achieved": bind["achieved"], "peak": bind["peak"],
+        "unit": bind["unit"], "frac": bind["frac"], "peak_source": bind["peak_source"],
         "traffic": None,
+        "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
+        "other_roof": other,
+        "algorithmic_flops_per_step": flops, "algorithmic_bytes_per_step": nbytes,
         "share_of_step": prof["gemm_ms"] / prof_step_ms,
         "launches": prof["gemm_launches"],
         "qr_ms_per_step": prof["qr_ms"],
-        "measured_on": "one extra eager step with per-launch CUDA events (ms %.0f)" % prof_step_ms,
+        "measured_on": "one extra eager step with per-launch CUDA events on the library's stream (ms %.0f)"
+                       % prof_step_ms,
     }
     cpu = None
     if not args.no_cpu_baseline and world == 1:

@@ -234,7 +234,9 @@ int64_t pepsvmc_launch_count(const pepsvmc_ctx* ctx);
  * on the context's stream (adds about a microsecond of host time per launch).
  * pepsvmc_set_profiling resets the counters.  pepsvmc_get_profile fills out[6]:
  * contraction launches, their algorithmic flops (2*M*N*K per chain), their
- * summed device time in ms, QR launches, their device time in ms, 0.         */
+ * summed device time in ms, QR launches, their device time in ms, and the
+ * contractions' algorithmic bytes (FP32 operands read once -- an operand shared by
+ * all chains once --, the result written once).                               */
 int pepsvmc_set_profiling(pepsvmc_ctx* ctx, int32_t on);
 int pepsvmc_get_profile(pepsvmc_ctx* ctx, double* out);
 /* The same counters per launch shape, as JSON text written to buf (len bytes):
@@ -249,6 +251,14 @@ int pepsvmc_get_profile_shapes(pepsvmc_ctx* ctx, char* buf, int64_t len);
  * heuristics then); pepsvmc_get_tuning writes the choices as JSON text:
  * [{"shape": "...", "choice": "f32_cfg3" | "tc_bn64", "candidate_ms": [...]}, ...]. */
 int pepsvmc_set_autotune(pepsvmc_ctx* ctx, int32_t on);
+
+/* Fix the kernel of every contraction of this context (kernel-level profiling and
+ * tests; the automatic choice computes the same products).  kind 0: automatic (the
+ * autotuner, or the size heuristic with autotuning off); 1: FP32 CUDA-core kernel
+ * with tile-table entry `tile` (0..5); 2: tcgen05 kernel with N tile `tile` (32, 64,
+ * 128, 256), mixed precisions only.  Drops a captured step graph.
+ * Errors: EINVAL (unknown kind or tile, or kind 2 at FP32).                        */
+int pepsvmc_set_contraction_kernel(pepsvmc_ctx* ctx, int32_t kind, int32_t tile);
 
 /* CUDA graphs (on by default): pepsvmc_energy_and_grad runs its first sample step
  * (sweep + measurement + sums) eagerly, then captures the step's launches once into

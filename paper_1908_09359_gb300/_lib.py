@@ -29,6 +29,7 @@ SYMBOLS = [
     "pepsvmc_get_chain_grad", "pepsvmc_amplitude", "pepsvmc_energy_and_grad", "pepsvmc_update",
     "pepsvmc_launch_count", "pepsvmc_set_profiling", "pepsvmc_get_profile", "pepsvmc_env3_left",
     "pepsvmc_env3_left_noalloc", "pepsvmc_get_profile_shapes", "pepsvmc_set_autotune", "pepsvmc_get_tuning",
+    "pepsvmc_set_contraction_kernel",
     "pepsvmc_set_graphs", "pepsvmc_set_proposal_params", "pepsvmc_get_proposal_params",
     "pepsvmc_proposal_logits", "pepsvmc_proposal_collect", "pepsvmc_proposal_dataset_size", "pepsvmc_proposal_load",
     "pepsvmc_proposal_train", "pepsvmc_set_proposal", "pepsvmc_learned_sweep", "pepsvmc_get_learned_trace",
@@ -90,6 +91,7 @@ def load(path: str | None = None):
         "pepsvmc_env3_left_noalloc": (C.c_int, [P, P, P, P, P, P] + [I32] * 9 + [P]),
         "pepsvmc_get_profile_shapes": (C.c_int, [P, C.c_char_p, I64]),
         "pepsvmc_set_autotune": (C.c_int, [P, I32]),
+        "pepsvmc_set_contraction_kernel": (C.c_int, [P, I32, I32]),
         "pepsvmc_set_graphs": (C.c_int, [P, I32]),
         "pepsvmc_set_proposal_params": (C.c_int, [P, D]),
         "pepsvmc_get_proposal_params": (C.c_int, [P, D]),

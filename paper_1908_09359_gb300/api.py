@@ -167,7 +167,7 @@ class PepsVMC:
         out = np.zeros(6)
         self._check(self.lib.pepsvmc_get_profile(self.ctx, _dp(out)))
         return dict(gemm_launches=int(out[0]), gemm_flops=out[1], gemm_ms=out[2],
-                    qr_launches=int(out[3]), qr_ms=out[4])
+                    qr_launches=int(out[3]), qr_ms=out[4], gemm_bytes=out[5])
 
     def env3_left(self, E, T, A, spins, B, out, dims):
         """Three-line environment step on device tensors (torch CUDA tensors or raw
@@ -229,6 +229,11 @@ class PepsVMC:
 
     def set_graphs(self, on=True):
         self._check(self.lib.pepsvmc_set_graphs(self.ctx, 1 if on else 0))
+
+    def set_contraction_kernel(self, kind, tile=0):
+        """kind: "auto", "f32" (tile 0..5) or "tc" (N tile 32, 64, 128, 256)."""
+        k = {"auto": 0, "f32": 1, "tc": 2}[kind]
+        self._check(self.lib.pepsvmc_set_contraction_kernel(self.ctx, k, int(tile)))
 
     def set_autotune(self, on=True):
         self._check(self.lib.pepsvmc_set_autotune(self.ctx, 1 if on else 0))

@@ -145,6 +145,9 @@ __device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_c
 // core matrix (r/8, kc) at ((r/8) * KC + kc) * 128 bytes, row r%8 at +16 (r%8).
 // Every thread first issues all of its global loads (16-byte loads where the operand
 // is K-contiguous, or row-contiguous with 4 rows per load), then converts and stores.
+// K-contiguous units are assigned so that eight consecutive lanes fill the eight rows
+// of one core matrix: a warp's 16-byte shared stores cover whole 128-byte core
+// matrices (no bank conflicts).
 template <int EB, int ROWS, bool X3>
 __device__ __forceinline__ void load_tile(uint8_t* tile, const float* base, long long s_row, long long s_k, int row0,
                                           int nrows, int k0, int K, int lo_off) {
@@ -156,7 +159,7 @@ __device__ __forceinline__ void load_tile(uint8_t* tile, const float* base, long
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       const int u = threadIdx.x + j * kThreads;
-      const int kc = u % KC, r = u / KC;
+      const int kc = (u >> 3) % KC, r = ((u >> 3) / KC) * 8 + (u & 7);
       const int row = row0 + r, k = k0 + kc * CE;
       const float* src = base + (long long)row * s_row + k;
       if (row < nrows && k + CE <= K && aligned16(src)) {
@@ -173,7 +176,7 @@ __device__ __forceinline__ void load_tile(uint8_t* tile, const float* base, long
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       const int u = threadIdx.x + j * kThreads;
-      const int kc = u % KC, r = u / KC;
+      const int kc = (u >> 3) % KC, r = ((u >> 3) / KC) * 8 + (u & 7);
       put16<EB, X3>(tile + ((r >> 3) * KC + kc) * 128 + (r & 7) * 16, f[j], lo_off);
     }
   } else if (s_row == 1 && (s_k & 3) == 0) {

@@ -229,7 +229,17 @@ struct pepsvmc_ctx {
   struct ShapeStat { long long n = 0; double flops = 0, ms = 0; };
   std::map<std::string, ShapeStat> shape_stats;
   std::vector<Pending> pending;
-  double prof_acc[6] = {0, 0, 0, 0, 0, 0};  // gemm launches, gemm flops, gemm ms, qr launches, qr ms, -
+  double prof_acc[6] = {0, 0, 0, 0, 0, 0};  // gemm launches, flops, ms, qr launches, qr ms, gemm bytes
+
+  // Algorithmic bytes of one contraction launch: every FP32 operand read once (an
+  // operand shared by all chains once, both spin slots of a selected site tensor), the
+  // result written once (read and written when accumulating).
+  double gemm_bytes(const GemmDesc& g) const {
+    const double a = (g.bsA ? (double)C : 1.0) * g.M * g.K;
+    const double b = (g.bsB ? (double)C : (g.sel ? 2.0 : 1.0)) * g.K * g.N;
+    const double c = (g.accumulate ? 2.0 : 1.0) * C * (double)g.M * g.N;
+    return 4.0 * (a + b + c);
+  }
 
   cudaEvent_t ev() {
     if (ev_pool.empty()) {
@@ -289,6 +299,7 @@ struct pepsvmc_ctx {
     if (prof) {
       prof_acc[0] += 1;
       prof_acc[1] += 2.0 * g.M * g.N * g.K * (double)C;
+      prof_acc[5] += gemm_bytes(g);
     }
     if (!prof) return launch_gemm(g);
     char key[96];
@@ -362,7 +373,9 @@ struct pepsvmc_ctx {
     tune_ms[key] = times;
     return cudaSuccess;
   }
+  int forced = -1;  // a choice code fixed by pepsvmc_set_contraction_kernel, or -1
   cudaError_t launch_gemm(const GemmDesc& g) {
+    if (forced >= 0) return run_choice(g, forced);
     if (!dry && (autotune || !tuned.empty())) {
       const std::string key = tune_key(g);
       auto it = tuned.find(key);
@@ -1636,6 +1649,18 @@ int pepsvmc_set_autotune(pepsvmc_ctx* x, int32_t on) {
   if (!x) return PEPSVMC_EINVAL;
   x->autotune = on != 0;
   if (!on) x->tuned.clear();
+  x->drop_graph();
+  x->eager_steps = 0;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_set_contraction_kernel(pepsvmc_ctx* x, int32_t kind, int32_t tile) {
+  if (!x) return PEPSVMC_EINVAL;
+  int choice = -1;
+  if (kind == 1 && tile >= 0 && tile < gemm_f32_num_configs()) choice = tile;
+  if (kind == 2 && x->tc_mode() && (tile == 32 || tile == 64 || tile == 128 || tile == 256)) choice = 100 + tile;
+  if (kind != 0 && choice < 0) return x->fail(PEPSVMC_EINVAL, "no such contraction kernel for this precision");
+  x->forced = choice;
   x->drop_graph();
   x->eager_steps = 0;
   return PEPSVMC_OK;

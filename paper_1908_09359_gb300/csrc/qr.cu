@@ -6,8 +6,9 @@
 // sign of each column so that diag(R) >= 0 makes Q unique for full-rank input,
 // so the truncated MPS does not depend on the QR routine used.
 //
-// One CTA per matrix; the matrix and the growing Q live in shared memory in
-// column-major order.  Reflector j: v = x + sign(x0)|x| e1, beta = 2/(v.v);
+// One CTA per matrix.  General form: the matrix and the growing Q live in shared
+// memory in column-major order; for rows <= 256, cols <= 32 a register-resident form
+// (below) is used instead.  Reflector j: v = x + sign(x0)|x| e1, beta = 2/(v.v);
 // a zero column gets no reflector and a zero diagonal.
 #include "common.cuh"
 
@@ -100,6 +101,119 @@ __global__ void __launch_bounds__(kQrThreads) qr_pos_kernel(const float* __restr
   }
 }
 
+// Register-resident form for rows <= 256, cols <= 32 (every bulk shape of D <= 8,
+// Dc <= 32): thread t holds row t of the matrix and of Q in registers, so a reflector
+// costs two block reductions instead of a pass over shared memory per column.  The
+// 32-wide reductions (w = v^T A over the remaining columns) run as a transposing warp
+// butterfly (31 shuffles leave column l's warp sum in lane l), then across the eight
+// warps through shared memory.  Same reflectors, signs and zero-column rule as above.
+constexpr int kQrRegCols = 32;
+
+__device__ __forceinline__ float warp_transpose_sum32(float (&p)[kQrRegCols]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool up = (lane & w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float send = up ? p[i] : p[i + w];
+      const float keep = up ? p[i + w] : p[i];
+      p[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return p[0];
+}
+
+// Sum over the block of p[k] for every k into tot_s[k] (shared); red: 8 x 32 floats.
+__device__ __forceinline__ void block_sum32(float (&p)[kQrRegCols], float* red, float* tot_s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float v = warp_transpose_sum32(p);
+  red[warp * 32 + lane] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < kQrThreads / 32; ++w) s += red[w * 32 + threadIdx.x];
+    tot_s[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Y and Q may be the same array (in-place QR): every row is read before any is written.
+__global__ void __launch_bounds__(kQrThreads) qr_pos_reg_kernel(const float* Y, long long bsY, long long yrs,
+                                                                long long ycs, float* Q, long long bsQ,
+                                                                long long qrs, long long qcs, int R, int C) {
+  __shared__ float red[kQrThreads];
+  __shared__ float tot[kQrRegCols];
+  __shared__ float beta[kQrRegCols];
+  __shared__ int flip[kQrRegCols];
+  __shared__ float x0s[2], nrm;  // x0 by parity of j: a zero column skips the reductions' barriers
+  const int t = threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  const float* Yb = Y + (long long)blockIdx.x * bsY;
+  float a[kQrRegCols], q[kQrRegCols], p[kQrRegCols];
+#pragma unroll
+  for (int k = 0; k < kQrRegCols; ++k) {
+    a[k] = (t < R && k < C) ? Yb[(long long)t * yrs + (long long)k * ycs] : 0.f;
+    q[k] = (t == k) ? 1.f : 0.f;
+  }
+  // factorisation: reflector j from column j, rows >= j; v overwrites a[j] of rows >= j
+#pragma unroll
+  for (int j = 0; j < kQrRegCols; ++j) {
+    if (j >= C) break;
+    float s = (t >= j) ? a[j] * a[j] : 0.f;
+    s = warp_sum(s);
+    if (lane == 0) red[warp] = s;
+    if (t == j) x0s[j & 1] = a[j];
+    __syncthreads();
+    if (t == 0) {
+      float n2 = 0.f;
+#pragma unroll
+      for (int w = 0; w < kQrThreads / 32; ++w) n2 += red[w];
+      nrm = sqrtf(n2);
+    }
+    __syncthreads();
+    const float alpha = nrm, x0 = x0s[j & 1];
+    const float sg = (x0 >= 0.f) ? 1.f : -1.f;
+    const float bj = alpha == 0.f ? 0.f : 1.f / (alpha * (alpha + fabsf(x0)));
+    if (t == 0) {
+      beta[j] = bj;
+      flip[j] = (alpha != 0.f && sg > 0.f) ? 1 : 0;  // R_jj = -sign(x0)|x| < 0 -> negate column j of Q
+    }
+    if (bj == 0.f) continue;  // uniform over the block: zero column, no reflector
+    if (t == j) a[j] = x0 + sg * alpha;
+    const float v = (t >= j) ? a[j] : 0.f;
+#pragma unroll
+    for (int k = 0; k < kQrRegCols; ++k) p[k] = (k > j) ? v * a[k] : 0.f;
+    block_sum32(p, red, tot);
+#pragma unroll
+    for (int k = 0; k < kQrRegCols; ++k)
+      if (k > j) a[k] = fmaf(-bj * tot[k], v, a[k]);
+  }
+  __syncthreads();
+  // thin Q = H_0 ... H_{C-1} [I; 0], accumulated backwards; H_j touches rows >= j and,
+  // at that point, only columns >= j of Q
+#pragma unroll
+  for (int j = kQrRegCols - 1; j >= 0; --j) {
+    if (j >= C) continue;
+    const float bj = beta[j];
+    if (bj == 0.f) continue;
+    const float v = (t >= j) ? a[j] : 0.f;
+#pragma unroll
+    for (int k = 0; k < kQrRegCols; ++k) p[k] = (k >= j) ? v * q[k] : 0.f;
+    block_sum32(p, red, tot);
+#pragma unroll
+    for (int k = 0; k < kQrRegCols; ++k)
+      if (k >= j) q[k] = fmaf(-bj * tot[k], v, q[k]);
+  }
+  if (t < R) {
+    float* Qb = Q + (long long)blockIdx.x * bsQ;
+#pragma unroll
+    for (int k = 0; k < kQrRegCols; ++k)
+      if (k < C) Qb[(long long)t * qrs + (long long)k * qcs] = flip[k] ? -q[k] : q[k];
+  }
+}
+
 }  // namespace
 
 cudaError_t qr_pos_batched(const float* Y, long long bsY, long long yrs, long long ycs, float* Q,
@@ -107,6 +221,10 @@ cudaError_t qr_pos_batched(const float* Y, long long bsY, long long yrs, long lo
                            cudaStream_t st) {
   if (g_dry_run || batch <= 0) return cudaSuccess;
   if (cols > kQrMaxCols || rows < cols || cols <= 0) return cudaErrorInvalidValue;
+  if (rows <= kQrThreads && cols <= kQrRegCols) {
+    qr_pos_reg_kernel<<<batch, kQrThreads, 0, st>>>(Y, bsY, yrs, ycs, Q, bsQ, qrs, qcs, rows, cols);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)2 * rows * cols * sizeof(float);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {

@@ -28,7 +28,14 @@ def main():
     p.add_argument("--chains", type=int, default=None)
     p.add_argument("--reps", type=int, default=10)
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "tf32", "bf16x3"])
+    p.add_argument("--kernel", default="auto",
+                   help="auto, or f32:CFG / tc:BN to fix every contraction's kernel")
     a = p.parse_args()
+
+    def fix_kernel(ctx):
+        if a.kernel != "auto":
+            kind, tile = a.kernel.split(":")
+            ctx.set_contraction_kernel(kind, int(tile))
     w = inputs.workload(a.workload, n_chains=1)
     n = a.chains or inputs.WORKLOADS[a.workload]["n_chains"]
     D, chi = w["D"], w["chi"]
@@ -38,6 +45,7 @@ def main():
         ctx = api.PepsVMC(wl["Ly"], wl["Lx"], D, chi, n, wl["tensors"], wl["sketch"], J1=wl["J1"], J2=wl["J2"],
                           seed=1, precision=prec)
         ctx.set_spins(wl["spins"])
+        fix_kernel(ctx)
         ctx.energy_and_grad(1, want_samples=False, want_grad=False)
         ctx.set_profiling(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -54,9 +62,14 @@ def main():
             tf = r["flops"] / (r["ms"] / 1e3) / 1e12 if r["ms"] > 0 else 0.0
             print(f'{r["shape"]:32s} launches {r["launches"]:7d}  ms {r["ms"]:10.1f}  '
                   f'share {r["ms"] / total:6.3f}  TFLOP/s {tf:7.2f}')
+        picks = {}
+        for t in ctx.get_tuning():
+            picks[t["choice"]] = picks.get(t["choice"], 0) + 1
+        print("autotuner choices (kernel: shapes):", json.dumps(picks, sort_keys=True))
         ctx.close()
         return
     ctx = api.PepsVMC(w["Ly"], w["Lx"], D, chi, n, w["tensors"], w["sketch"], seed=1, precision=prec)
+    fix_kernel(ctx)
     g = torch.Generator(device="cuda").manual_seed(0)
     r = lambda *s: torch.randn(*s, generator=g, device="cuda")  # noqa: E731
     E, T, B = r(n, chi, D, chi), r(n, chi, D, chi), r(n, chi, D, chi)
@@ -76,7 +89,7 @@ def main():
     ms = e0.elapsed_time(e1) / a.reps
     flops = 2.0 * (2 * chi ** 3 * D ** 2 + chi ** 2 * D ** 4) * n
     print(json.dumps({"case": a.case, "workload": a.workload, "precision": a.precision, "chains": n,
-                      "ms_per_step": ms,
+                      "kernel": a.kernel, "ms_per_step": ms,
                       "tflops": flops / (ms / 1e3) / 1e12}))
     ctx.close()
 

@@ -51,3 +51,34 @@ def test_env3_tensor_cores_match_oracle(torch_mod, precision, dims):
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err <= TOL[precision], err
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [1, 2, 3])
+@pytest.mark.parametrize("bn", [32, 64, 128, 256])
+def test_env3_every_tile_width_matches_oracle(torch_mod, precision, bn):
+    """Each tcgen05 tile width fixed for all three products of the step (the autotuner
+    would otherwise pick per shape), at the 24x24 bulk shapes with 300 chains."""
+    torch = torch_mod
+    from paper_1908_09359_gb300 import api, inputs
+    dims = (300, 32, 32, 32, 32, 8, 8, 8, 8)
+    n, cT, cB, cT2, cB2, Dl, Dr, Du, Dd = dims
+    ctx = api.PepsVMC(8, 8, 8, 32, n, inputs.peps_tensors(8, 8, 8, 1), inputs.sketch(8, 32, 8, 1),
+                      seed=1, precision=precision)
+    ctx.set_contraction_kernel("tc", bn)
+    rng = np.random.default_rng(bn + precision)
+    f32 = lambda *s: rng.standard_normal(s).astype(np.float32)  # noqa: E731
+    E, T, A, B = f32(n, cT, Dl, cB), f32(n, cT, Du, cT2), f32(2, Dl, Dr, Du, Dd), f32(n, cB, Dd, cB2)
+    spins = rng.choice(np.array([1, -1], dtype=np.int8), n)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    out = torch.empty((n, cT2, Dr, cB2), dtype=torch.float32, device="cuda")
+    ctx.env3_left(dev(E), dev(T), dev(A.transpose(0, 1, 3, 2, 4)), dev(spins), dev(B), out, dims)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for i in list(range(0, n, 25)) + [n - 1]:
+        ref = vmc.env3_left(E[i].astype(np.float64), T[i].astype(np.float64),
+                            A[0 if spins[i] > 0 else 1].astype(np.float64), B[i].astype(np.float64))
+        err = np.linalg.norm(got[i] - ref) / np.linalg.norm(ref)
+        assert err <= TOL[precision], (i, err)
+    with pytest.raises(Exception):
+        ctx.set_contraction_kernel("tc", 48)
+    ctx.close()
