@@ -17,8 +17,10 @@ whose bond spectra decay as after a simple-update initialisation (bond weights
 lambda_i = exp(-i), App. A), at the shapes of the 8x8 and 24x24 workloads.  With iid
 N(0,1) tensors at truncated Dc the quantities are ill-conditioned: the same oracle
 code run in float32 (numpy/LAPACK) deviates from float64 by up to 2.2e-4 on sweep
-ratios and ~2e-6 on E_loc at sampled 8x8 configurations, so those cases are checked
-against bounds derived from that deviation (RATIO_TOL_IID, ELOC_TOL_IID).
+ratios and ~2e-6 on E_loc at sampled 8x8 configurations; with the QR of the fit written
+as plain float32 Householder (the GPU's algorithm) G moves by up to 2.2e-4 norm-wise
+between summation orders of the reflector dot products alone.  Those cases are checked
+against bounds derived from these deviations (RATIO_TOL_IID, ELOC_TOL_IID, GRAD_TOL_IID).
 """
 import os
 import sys
@@ -41,6 +43,7 @@ LOGPSI_TOL = 1e-4
 # iid N(0,1) tensors at truncated Dc: about twice the float32 oracle's own deviation
 RATIO_TOL_IID = 5e-4
 ELOC_TOL_IID = 1e-4
+GRAD_TOL_IID = 5e-4
 DECAY = 1.0
 
 
@@ -128,7 +131,7 @@ def test_amplitude_parity_finite_dc(api, row):
 
 @pytest.mark.parametrize("case", ["4x4_exact", "8x8_structured", "6x6_j1j2_structured", "8x8_iid_sampled"])
 def test_measure_parity(api, case):
-    eloc_tol = ELOC_TOL
+    eloc_tol, grad_tol = ELOC_TOL, GRAD_TOL
     n_fit = 3
     if case == "4x4_exact":
         w, n_fit = small_workload(4, 4, 2, 4, seed=8), 1
@@ -142,7 +145,7 @@ def test_measure_parity(api, case):
     else:
         w = inputs.workload("peps_8x8", n_chains=8)
         sp = golden.load("peps_8x8")
-        eloc_tol = ELOC_TOL_IID
+        eloc_tol, grad_tol = ELOC_TOL_IID, GRAD_TOL_IID
     g = grid_of(w)
     ctx = ctx_for(api, w, len(sp), n_fit=n_fit)
     ctx.set_spins(sp)
@@ -152,7 +155,7 @@ def test_measure_parity(api, case):
         assert abs(e[c] - r["eloc"]) <= eloc_tol * r["eloc_scale"], (c, e[c], r["eloc"])
         assert sg[c] == r["sign"]
         assert abs(lp[c] - r["logpsi"]) <= LOGPSI_TOL
-        check_grad(ctx.chain_grad(c), flat_G(r["G"]))
+        check_grad(ctx.chain_grad(c), flat_G(r["G"]), grad_tol)
     ctx.close()
 
 
