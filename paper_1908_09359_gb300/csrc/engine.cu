@@ -119,6 +119,7 @@ struct pepsvmc_ctx {
   float *envL = nullptr, *envR = nullptr, *envRf = nullptr;
   float *l3[2] = {}, *fl = nullptr;
   float *tmp1 = nullptr, *tmp2 = nullptr;
+  float *tmp3 = nullptr, *tmp4 = nullptr;  // the two shared four-line intermediates Y(f1 = 0, 1)
   float *R4 = nullptr, *l4[2] = {}, *fl4 = nullptr, *ptop[2] = {}, *pbot[2] = {};
   float* G = nullptr;
   double *eloc = nullptr, *den = nullptr, *logpsi = nullptr;
@@ -462,11 +463,34 @@ struct pepsvmc_ctx {
     for (int i = 0; i < 3; ++i) PV_CUDA(gemm(g[i]));
     return cudaSuccess;
   }
+  // Left step for the configuration and, when out1 is given, with the spin of the site
+  // flipped: the first product E . T does not depend on the spin and is done once;
+  // tmp1 keeps it afterwards (delta3_after_left3 reads it).
+  cudaError_t left3_pair(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
+                         const SiteOp& a, const float* B, long long bsB, int cB2, float* out0, float* out1,
+                         long long bsO) {
+    GemmDesc g[3];
+    const Env3Dims d{cT, cB, cT2, cB2, a.Dl, a.Dr, a.Du, a.Dd};
+    env3_left_descs(g, d, E, bsE, T, bsT, a.lurd, a.size, spins + a.spin, (long long)Ly * Lx, 0, B, bsB, out0, bsO,
+                    tmp1, tmp2, SI);
+    for (int i = 0; i < 3; ++i) PV_CUDA(gemm(g[i]));
+    if (!out1) return cudaSuccess;
+    env3_left_descs(g, d, E, bsE, T, bsT, a.lurd, a.size, spins + a.spin, (long long)Ly * Lx, 1, B, bsB, out1, bsO,
+                    tmp1, tmp2, SI);
+    PV_CUDA(gemm(g[1]));
+    return gemm(g[2]);
+  }
 
   // Three-line right step: E (cT2,Dr,cB2) -> out (cT,Dl,cB).
   cudaError_t right3(const float* E, long long bsE, int cT2, int cB2, const float* T, long long bsT, int cT,
                      const SiteOp& a, int flip, const float* B, long long bsB, int cB, float* out,
                      long long bsO) {
+    PV_CUDA(right3_head(E, bsE, cT2, cB2, T, bsT, cT, a, flip));
+    return right3_tail(a, cT, cB2, B, bsB, cB, out, bsO);
+  }
+  // First two products of the right step: tmp2 [cT][Dl][Dd][cB2] = T . E . a (E on the right).
+  cudaError_t right3_head(const float* E, long long bsE, int cT2, int cB2, const float* T, long long bsT, int cT,
+                          const SiteOp& a, int flip, bool first = true) {
     const int Dl = a.Dl, Dr = a.Dr, Du = a.Du, Dd = a.Dd;
     GemmDesc g;
     g.M = cT * Du; g.N = Dr * cB2; g.K = cT2;
@@ -475,7 +499,7 @@ struct pepsvmc_ctx {
     g.C = tmp1; g.bsC = SI;
     g.cm2 = Du; g.sCm1 = (long long)cB2 * Du * Dr; g.sCm2 = Dr;
     g.cn2 = cB2; g.sCn1 = 1; g.sCn2 = (long long)Du * Dr;
-    PV_CUDA(gemm(g));
+    if (first) PV_CUDA(gemm(g));  // else tmp1 still holds T . E from the previous call
     GemmDesc h;
     h.M = cT * cB2; h.N = Dl * Dd; h.K = Du * Dr;
     h.A = tmp1; h.sAm = (long long)Du * Dr; h.sAk = 1; h.bsA = SI;
@@ -483,12 +507,54 @@ struct pepsvmc_ctx {
     h.C = tmp2; h.bsC = SI;
     h.cm2 = cB2; h.sCm1 = (long long)Dl * Dd * cB2; h.sCm2 = 1;
     h.cn2 = Dd; h.sCn1 = (long long)Dd * cB2; h.sCn2 = cB2;
-    PV_CUDA(gemm(h));
+    return gemm(h);
+  }
+  // Right step for the configuration and with the spin of the site flipped, sharing T . E.
+  cudaError_t right3_pair(const float* E, long long bsE, int cT2, int cB2, const float* T, long long bsT, int cT,
+                          const SiteOp& a, const float* B, long long bsB, int cB, float* out0, float* out1,
+                          long long bsO) {
+    PV_CUDA(right3_head(E, bsE, cT2, cB2, T, bsT, cT, a, 0));
+    PV_CUDA(right3_tail(a, cT, cB2, B, bsB, cB, out0, bsO));
+    PV_CUDA(right3_head(E, bsE, cT2, cB2, T, bsT, cT, a, 1, false));
+    return right3_tail(a, cT, cB2, B, bsB, cB, out1, bsO);
+  }
+  // Last product of the right step: out (cT,Dl,cB) = tmp2 [cT][Dl][Dd][cB2] . B (cB,Dd,cB2).
+  cudaError_t right3_tail(const SiteOp& a, int cT, int cB2, const float* B, long long bsB, int cB, float* out,
+                          long long bsO) {
+    const int Dl = a.Dl, Dd = a.Dd;
     GemmDesc q;
     q.M = cT * Dl; q.N = cB; q.K = Dd * cB2;
     q.A = tmp2; q.sAm = (long long)Dd * cB2; q.sAk = 1; q.bsA = SI;
     q.B = B; q.sBk = 1; q.sBn = (long long)Dd * cB2; q.bsB = bsB;
     q.C = out; q.bsC = bsO; q.sCm1 = cB; q.sCn1 = 1;
+    return gemm(q);
+  }
+  // Last product of the left step from the fit's intermediate: after proj3, tmp2 holds
+  // [cV][Dd][cT2][Dr] = L . T . a, so the new left environment of the fitted site V
+  // (cV,Dd,cV2) is out (cT2,Dr,cV2) = tmp2 . V -- the step's first two products are
+  // the optimal-site products already done.
+  cudaError_t left3_tail_after_proj(const SiteOp& a, int cV, int cT2, const float* V, long long bsV, int cV2,
+                                    float* out, long long bsO) {
+    const int Dr = a.Dr, Dd = a.Dd;
+    GemmDesc q;
+    q.M = cT2 * Dr; q.N = cV2; q.K = cV * Dd;
+    q.A = tmp2; q.sAm = 1; q.sAk = (long long)cT2 * Dr; q.bsA = SI;
+    q.B = V; q.sBk = cV2; q.sBn = 1; q.bsB = bsV;
+    q.C = out; q.bsC = bsO; q.sCm1 = cV2; q.sCn1 = 1;
+    return gemm(q);
+  }
+  // Optimal site contracted from the right (for right-to-left half-sweeps): tmp2
+  // [cT][Dl][Dd][cV2] = T . R . a as in the right step, then Y (cV,Dd,cV2) = L . tmp2;
+  // right3_tail then gives the new right environment without repeating those products.
+  cudaError_t proj3_right(const float* Lf, long long bsL, int cT, int cV, const float* T, long long bsT, int cT2,
+                          const SiteOp& a, const float* Rf, long long bsR, int cV2, float* Y, long long bsY) {
+    PV_CUDA(right3_head(Rf, bsR, cT2, cV2, T, bsT, cT, a, 0));
+    const int Dl = a.Dl, Dd = a.Dd;
+    GemmDesc q;
+    q.M = Dd * cV2; q.N = cV; q.K = cT * Dl;
+    q.A = tmp2; q.sAm = 1; q.sAk = (long long)Dd * cV2; q.bsA = SI;
+    q.B = Lf; q.sBk = cV; q.sBn = 1; q.bsB = bsL;
+    q.C = Y; q.bsC = bsY; q.sCm1 = 1; q.sCn1 = (long long)Dd * cV2;
     return gemm(q);
   }
 
@@ -520,19 +586,11 @@ struct pepsvmc_ctx {
     return gemm(q);
   }
 
-  // Defect network (Eq. (7)) divided by Psi: G[l][r][u][d] = L.T.B.R / den.
-  cudaError_t delta3(const float* Lf, long long bsL, int cT, int cB, const float* T, long long bsT, int cT2,
-                     const SiteOp& a, const float* B, long long bsB, int cB2, const float* Rf, long long bsR,
-                     const double* dn, float* Gout, long long bsG) {
+  // Defect network (Eq. (7)) divided by Psi, G[l][r][u][d] = L.T.B.R / den, after
+  // left3_pair on the same site: tmp1 holds L . T as [cB][cT2][Dl][Du].
+  cudaError_t delta3_after_left3(int cB, int cT2, const SiteOp& a, const float* B, long long bsB, int cB2,
+                                 const float* Rf, long long bsR, const double* dn, float* Gout, long long bsG) {
     const int Dl = a.Dl, Dr = a.Dr, Du = a.Du, Dd = a.Dd;
-    GemmDesc g;
-    g.M = Dl * cB; g.N = Du * cT2; g.K = cT;
-    g.A = Lf; g.sAm = 1; g.sAk = (long long)Dl * cB; g.bsA = bsL;
-    g.B = T; g.sBk = (long long)Du * cT2; g.sBn = 1; g.bsB = bsT;
-    g.C = tmp1; g.bsC = SI;
-    g.cm2 = cB; g.sCm1 = (long long)Du * cB * cT2; g.sCm2 = cT2;
-    g.cn2 = cT2; g.sCn1 = (long long)cB * cT2; g.sCn2 = 1;
-    PV_CUDA(gemm(g));
     GemmDesc p;
     p.M = cB * Dd; p.N = cT2 * Dr; p.K = cB2;
     p.A = B; p.sAm = cB2; p.sAk = 1; p.bsA = bsB;
@@ -543,7 +601,7 @@ struct pepsvmc_ctx {
     PV_CUDA(gemm(p));
     GemmDesc q;
     q.M = Dl * Du; q.N = Dd * Dr; q.K = cB * cT2;
-    q.A = tmp1; q.sAm = (long long)cB * cT2; q.sAk = 1; q.bsA = SI;
+    q.A = tmp1; q.sAm = 1; q.sAk = (long long)Dl * Du; q.bsA = SI;
     q.B = tmp2; q.sBk = (long long)Dd * Dr; q.sBn = 1; q.bsB = SI;
     q.C = Gout; q.bsC = bsG;
     q.cm2 = Du; q.sCm1 = (long long)Dr * Du * Dd; q.sCm2 = Dd;
@@ -552,39 +610,57 @@ struct pepsvmc_ctx {
     return gemm(q);
   }
 
-  // Four-line left step of rows (k, k+1): E (cT,D1l,D2l,cB) -> out (cT2,D1r,D2r,cB2).
+  // Four-line left step of rows (k, k+1): E (cT,D1l,D2l,cB) -> out (cT2,D1r,D2r,cB2),
+  // as four products: (1) E . T -> X; (2) X . a1 -> Y; (3) Y . a2 -> Z; (4) Z . B -> out.
+  // Only (2) depends on the spin of (k, m) and only (3) on that of (k+1, m), so the
+  // measurement shares (1) over its four spin-flip variants and (2) over pairs of them.
   cudaError_t left4(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
                     const SiteOp& a1, int f1, const SiteOp& a2, int f2, const float* B, long long bsB, int cB2,
                     float* out, long long bsO) {
-    const int D1l = a1.Dl, D1r = a1.Dr, Du1 = a1.Du, Dd1 = a1.Dd;
-    const int D2l = a2.Dl, D2r = a2.Dr, Dd2 = a2.Dd;
+    PV_CUDA(left4_x(E, bsE, cT, cB, T, bsT, cT2, a1, a2, tmp1));
+    PV_CUDA(left4_y(tmp1, cB, cT2, a1, f1, a2, tmp2));
+    return left4_zw(tmp2, cB, cT2, a1, a2, f2, B, bsB, cB2, out, bsO, tmp1);
+  }
+  // (1): X [(D2l,cB)][cT2][D1l][Du1] = E . T over cT.
+  cudaError_t left4_x(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
+                      const SiteOp& a1, const SiteOp& a2, float* X) {
+    const int D1l = a1.Dl, Du1 = a1.Du, D2l = a2.Dl;
     GemmDesc g;
     g.M = D1l * D2l * cB; g.N = Du1 * cT2; g.K = cT;
     g.A = E; g.sAm = 1; g.sAk = (long long)D1l * D2l * cB; g.bsA = bsE;
     g.B = T; g.sBk = (long long)Du1 * cT2; g.sBn = 1; g.bsB = bsT;
-    g.C = tmp1; g.bsC = SI;
+    g.C = X; g.bsC = SI;
     g.cm2 = D2l * cB; g.sCm1 = Du1; g.sCm2 = (long long)cT2 * D1l * Du1;
     g.cn2 = cT2; g.sCn1 = 1; g.sCn2 = (long long)D1l * Du1;
-    PV_CUDA(gemm(g));
+    return gemm(g);
+  }
+  // (2): Y [(cB,cT2)][D1r][D2l][Dd1] = X . a1 (spin of (k, m), flipped when f1).
+  cudaError_t left4_y(const float* X, int cB, int cT2, const SiteOp& a1, int f1, const SiteOp& a2, float* Y) {
+    const int D1l = a1.Dl, D1r = a1.Dr, Du1 = a1.Du, Dd1 = a1.Dd, D2l = a2.Dl;
     GemmDesc h;
     h.M = D2l * cB * cT2; h.N = D1r * Dd1; h.K = D1l * Du1;
-    h.A = tmp1; h.sAm = (long long)D1l * Du1; h.sAk = 1; h.bsA = SI;
+    h.A = X; h.sAm = (long long)D1l * Du1; h.sAk = 1; h.bsA = SI;
     sel(h, a1, a1.lurd, f1); h.sBk = (long long)D1r * Dd1; h.sBn = 1;
-    h.C = tmp2; h.bsC = SI;
+    h.C = Y; h.bsC = SI;
     h.cm2 = cB * cT2; h.sCm1 = Dd1; h.sCm2 = (long long)D1r * D2l * Dd1;
     h.cn2 = Dd1; h.sCn1 = (long long)D2l * Dd1; h.sCn2 = 1;
-    PV_CUDA(gemm(h));
+    return gemm(h);
+  }
+  // (3) and (4): Z = Y . a2 (spin of (k+1, m), flipped when f2) into scratch, out = Z . B.
+  cudaError_t left4_zw(const float* Y, int cB, int cT2, const SiteOp& a1, const SiteOp& a2, int f2,
+                       const float* B, long long bsB, int cB2, float* out, long long bsO, float* scratch) {
+    const int D1r = a1.Dr, Dd1 = a1.Dd, D2l = a2.Dl, D2r = a2.Dr, Dd2 = a2.Dd;
     GemmDesc q;
     q.M = cB * cT2 * D1r; q.N = D2r * Dd2; q.K = D2l * Dd1;
-    q.A = tmp2; q.sAm = (long long)D2l * Dd1; q.sAk = 1; q.bsA = SI;
+    q.A = Y; q.sAm = (long long)D2l * Dd1; q.sAk = 1; q.bsA = SI;
     sel(q, a2, a2.lurd, f2); q.sBk = (long long)D2r * Dd2; q.sBn = 1;
-    q.C = tmp1; q.bsC = SI;
+    q.C = scratch; q.bsC = SI;
     q.cm2 = cT2 * D1r; q.sCm1 = Dd2; q.sCm2 = (long long)D2r * cB * Dd2;
     q.cn2 = Dd2; q.sCn1 = (long long)cB * Dd2; q.sCn2 = 1;
     PV_CUDA(gemm(q));
     GemmDesc w;
     w.M = cT2 * D1r * D2r; w.N = cB2; w.K = cB * Dd2;
-    w.A = tmp1; w.sAm = (long long)cB * Dd2; w.sAk = 1; w.bsA = SI;
+    w.A = scratch; w.sAm = (long long)cB * Dd2; w.sAk = 1; w.bsA = SI;
     w.B = B; w.sBk = cB2; w.sBn = 1; w.bsB = bsB;
     w.C = out; w.bsC = bsO; w.sCm1 = cB2; w.sCn1 = 1;
     return gemm(w);
@@ -714,8 +790,7 @@ struct pepsvmc_ctx {
                         vb[m + 1], Vs, S));
           if (m < L - 1) {
             PV_CUDA(qr(Vs, S, vb[m + 1], 1, Vs, S, vb[m + 1], 1, vb[m] * p[m], vb[m + 1], C));
-            PV_CUDA(left3(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], 0, Vs, S,
-                          vb[m + 1], envLp(m + 1), S));
+            PV_CUDA(left3_tail_after_proj(a[m], vb[m], tb[m + 1], Vs, S, vb[m + 1], envLp(m + 1), S));
             PV_CUDA(norm2(envLp(m + 1), S, tb[m + 1] * a[m].Dr * vb[m + 1], nullptr, 0, nullptr, 0, exps));
           }
         }
@@ -726,13 +801,12 @@ struct pepsvmc_ctx {
           const float* Rin = m == L - 1 ? ones : envRp(m + 1);
           const long long bsR = m == L - 1 ? 1 : S;
           float* Vs = Vb + m * vss;
-          PV_CUDA(proj3(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], Rin, bsR,
-                        vb[m + 1], Vs, S));
+          PV_CUDA(proj3_right(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], Rin,
+                              bsR, vb[m + 1], Vs, S));
           if (m > 0) {
             const int rows = p[m] * vb[m + 1];
             PV_CUDA(qr(Vs, S, 1, rows, Vs, S, 1, rows, rows, vb[m], C));
-            PV_CUDA(right3(Rin, bsR, tb[m + 1], vb[m + 1], Tin.site(m), Tin.chain_stride, tb[m], a[m], 0, Vs, S,
-                           vb[m], envRp(m), S));
+            PV_CUDA(right3_tail(a[m], tb[m], vb[m + 1], Vs, S, vb[m], envRp(m), S));
             PV_CUDA(norm2(envRp(m), S, tb[m] * a[m].Dl * vb[m]));
           }
         }
@@ -774,20 +848,16 @@ struct pepsvmc_ctx {
         const bool edge = (m == Lxo - 1);
         const float* Ein = edge ? ones : envRp(m + 1);
         const long long bsE = edge ? 1 : S;
-        PV_CUDA(right3(Ein, bsE, tb[m + 1], bb[m + 1], T.site(m), T.chain_stride, tb[m], a[m], 0, B.site(m),
-                       B.chain_stride, bb[m], envRp(m), S));
-        PV_CUDA(right3(Ein, bsE, tb[m + 1], bb[m + 1], T.site(m), T.chain_stride, tb[m], a[m], 1, B.site(m),
-                       B.chain_stride, bb[m], envRfp(m), S));
+        PV_CUDA(right3_pair(Ein, bsE, tb[m + 1], bb[m + 1], T.site(m), T.chain_stride, tb[m], a[m], B.site(m),
+                            B.chain_stride, bb[m], envRp(m), envRfp(m), S));
         const int n = tb[m] * a[m].Dl * bb[m];
         PV_CUDA(norm2(envRp(m), S, n, envRfp(m), n));
       }
       const float* Lin = ones;
       long long bsL = 1;
       for (int m = 0; m + 1 < Lxo; ++m) {
-        PV_CUDA(left3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], 0, B.site(m),
-                      B.chain_stride, bb[m + 1], l3[1], S));
-        PV_CUDA(left3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], 1, B.site(m),
-                      B.chain_stride, bb[m + 1], fl, S));
+        PV_CUDA(left3_pair(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], B.site(m),
+                           B.chain_stride, bb[m + 1], l3[1], fl, S));
         MetropolisArgs ma{};
         ma.cur = l3[1]; ma.bs_cur = S;
         ma.Rcur = envRp(m + 1); ma.bs_Rcur = S;
@@ -926,10 +996,8 @@ struct pepsvmc_ctx {
         const bool edge = (m == Lx - 1);
         const float* Ein = edge ? ones : envRp(m + 1);
         const long long bsE = edge ? 1 : S;
-        PV_CUDA(right3(Ein, bsE, tb[m + 1], bb[m + 1], T.site(m), T.chain_stride, tb[m], a[m], 0, B.site(m),
-                       B.chain_stride, bb[m], envRp(m), S));
-        PV_CUDA(right3(Ein, bsE, tb[m + 1], bb[m + 1], T.site(m), T.chain_stride, tb[m], a[m], 1, B.site(m),
-                       B.chain_stride, bb[m], envRfp(m), S));
+        PV_CUDA(right3_pair(Ein, bsE, tb[m + 1], bb[m + 1], T.site(m), T.chain_stride, tb[m], a[m], B.site(m),
+                            B.chain_stride, bb[m], envRp(m), envRfp(m), S));
         const int n = tb[m] * a[m].Dl * bb[m];
         PV_CUDA(norm2(envRp(m), S, n, envRfp(m), n));
       }
@@ -942,16 +1010,13 @@ struct pepsvmc_ctx {
         const long long bsR = edge ? 1 : S;
         float* cur = l3[(m + 1) % 2];
         const int n = tb[m + 1] * a[m].Dr * bb[m + 1];
-        PV_CUDA(left3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], 0, B.site(m),
-                      B.chain_stride, bb[m + 1], cur, S));
+        PV_CUDA(left3_pair(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], B.site(m),
+                           B.chain_stride, bb[m + 1], cur, edge ? nullptr : fl, S));
         PV_CUDA(dot(cur, S, Rin, bsR, n, den));
-        if (!edge) {
-          PV_CUDA(left3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], 1, B.site(m),
-                        B.chain_stride, bb[m + 1], fl, S));
+        if (!edge)
           PV_CUDA(ratio(fl, S, envRfp(m + 1), S, n, a[m].spin, a[m + 1].spin, 0.5 * cfg.J1, (long long)k * Lx + m));
-        }
-        PV_CUDA(delta3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], B.site(m),
-                       B.chain_stride, bb[m + 1], Rin, bsR, den, G + site_half_off[(size_t)k * Lx + m], Ph));
+        PV_CUDA(delta3_after_left3(bb[m], tb[m + 1], a[m], B.site(m), B.chain_stride, bb[m + 1], Rin, bsR, den,
+                                   G + site_half_off[(size_t)k * Lx + m], Ph));
         if (!edge) {
           PV_CUDA(norm2(cur, S, n, nullptr, 0, nullptr, 0, k == kstar ? exps : nullptr));
         } else if (k == kstar) {
@@ -997,23 +1062,31 @@ struct pepsvmc_ctx {
         return left4(Ein, bsE, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a1[m], f1, a2[m], f2,
                      B.site(m), B.chain_stride, bb[m + 1], out, S4);
       };
-      PV_CUDA(step(Lin, bsL, 0, 0, cur));
+      // the four variants of this column from Lin share X = Lin . T and Y(f1) = X . a1
+      auto from_y = [&](const float* Y, int f2, float* out) {
+        return left4_zw(Y, bb[m], tb[m + 1], a1[m], a2[m], f2, B.site(m), B.chain_stride, bb[m + 1], out, S4,
+                        tmp1);
+      };
+      PV_CUDA(left4_x(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a1[m], a2[m], tmp1));
+      PV_CUDA(left4_y(tmp1, bb[m], tb[m + 1], a1[m], 0, a2[m], tmp3));
+      PV_CUDA(left4_y(tmp1, bb[m], tb[m + 1], a1[m], 1, a2[m], tmp4));
+      PV_CUDA(from_y(tmp3, 0, cur));
       PV_CUDA(dot(cur, S4, Rin, bsR, n, den));
-      PV_CUDA(step(Lin, bsL, 1, 1, fl4));
+      PV_CUDA(from_y(tmp4, 1, fl4));
       PV_CUDA(ratio(fl4, S4, Rin, bsR, n, a1[m].spin, a2[m].spin, 0.5 * cfg.J1, (long long)Ly * Lx + k * Lx + m));
       float *Ptn = nullptr, *Pbn = nullptr;
       if (cfg.J2 != 0.0) {
+        if (!edge) {
+          Ptn = ptop[(m + 1) % 2];
+          Pbn = pbot[(m + 1) % 2];
+          PV_CUDA(from_y(tmp4, 0, Ptn));
+          PV_CUDA(from_y(tmp3, 1, Pbn));
+        }
         if (m >= 1) {
           PV_CUDA(step(Pt, S4, 0, 1, fl4));
           PV_CUDA(ratio(fl4, S4, Rin, bsR, n, a1[m - 1].spin, a2[m].spin, 0.5 * cfg.J2));
           PV_CUDA(step(Pb, S4, 1, 0, fl4));
           PV_CUDA(ratio(fl4, S4, Rin, bsR, n, a2[m - 1].spin, a1[m].spin, 0.5 * cfg.J2));
-        }
-        if (!edge) {
-          Ptn = ptop[(m + 1) % 2];
-          Pbn = pbot[(m + 1) % 2];
-          PV_CUDA(step(Lin, bsL, 1, 0, Ptn));
-          PV_CUDA(step(Lin, bsL, 0, 1, Pbn));
         }
       }
       if (!edge) PV_CUDA(norm2(cur, S4, n, Ptn, Ptn ? n : 0, Pbn, Pbn ? n : 0));
@@ -1344,6 +1417,8 @@ int setup(pepsvmc_ctx* x, const double* tensors, const double* sketch) {
   ALLOC(x->fl, C * x->S);
   ALLOC(x->tmp1, C * x->SI);
   ALLOC(x->tmp2, C * x->SI);
+  ALLOC(x->tmp3, C * x->SI);
+  ALLOC(x->tmp4, C * x->SI);
   ALLOC(x->R4, (long long)(Lx + 1) * C * x->S4);
   ALLOC(x->l4[0], C * x->S4);
   ALLOC(x->l4[1], C * x->S4);
