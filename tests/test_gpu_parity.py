@@ -2,8 +2,9 @@
 
 Tolerances of the FP32 path against the FP64 oracle (equal Dc, same truncation, same
 configurations):
-  * amplitude ratios and E_loc: 1e-5 relative; E_loc relative to the sum of the
-    magnitudes of its terms, ratios relative to max(|ratio|, 1);
+  * E_loc: 1e-5 relative to the sum of the magnitudes of its terms; the ratios that
+    enter it are checked through it; the sampler's ratios relative to max(|ratio|, 1)
+    against the float32 floor of the sweep (below);
   * G = Delta/Psi and the energy gradient: 1e-4 relative, norm-wise per chain, and
     element-wise against 1e-4 of the largest entry;
   * ln|Psi|: 1e-4 absolute (Psi is a product over every truncated row, so its
@@ -16,11 +17,15 @@ These hold where the contraction is well conditioned: at exact Dc, and on tensor
 whose bond spectra decay as after a simple-update initialisation (bond weights
 lambda_i = exp(-i), App. A), at the shapes of the 8x8 and 24x24 workloads.  With iid
 N(0,1) tensors at truncated Dc the quantities are ill-conditioned: the same oracle
-code run in float32 (numpy/LAPACK) deviates from float64 by up to 2.2e-4 on sweep
-ratios and ~2e-6 on E_loc at sampled 8x8 configurations; with the QR of the fit written
-as plain float32 Householder (the GPU's algorithm) G moves by up to 2.2e-4 norm-wise
-between summation orders of the reflector dot products alone.  Those cases are checked
-against bounds derived from these deviations (RATIO_TOL_IID, ELOC_TOL_IID, GRAD_TOL_IID).
+code run in float32 deviates from float64 by ~2e-6 on E_loc at sampled 8x8
+configurations, and with the fit's QR written as plain float32 Householder (the GPU's
+algorithm) sweep ratios move by 1.1e-3 to 3.4e-3 and G by 0.8e-4 to 2.2e-4 norm-wise
+between three summation orders of the reflector dot products alone
+(tests/float32_spread.py).  Even on the bond-decay tensors the sweep of the 8x8 shapes
+sits at the float32 floor: the same float32 runs give worst sweep-ratio deviations of
+7.8e-6, 8.5e-6 and 1.7e-5 (7.9e-6 with a float64 QR).  Those cases are checked against
+bounds of about twice the float32 spread (RATIO_TOL_SWEEP, RATIO_TOL_IID, ELOC_TOL_IID,
+GRAD_TOL_IID).
 """
 import os
 import sys
@@ -36,12 +41,12 @@ import make_sampled_configs as golden  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-RATIO_TOL = 1e-5
 ELOC_TOL = 1e-5
 GRAD_TOL = 1e-4
 LOGPSI_TOL = 1e-4
-# iid N(0,1) tensors at truncated Dc: about twice the float32 oracle's own deviation
-RATIO_TOL_IID = 5e-4
+# about twice the float32 oracle's own spread (tests/float32_spread.py)
+RATIO_TOL_SWEEP = 3.5e-5
+RATIO_TOL_IID = 7e-3
 ELOC_TOL_IID = 1e-4
 GRAD_TOL_IID = 5e-4
 DECAY = 1.0
@@ -191,9 +196,10 @@ def _sweep_parity(api, w, start, seed, t, chains, ratio_tol):
 
 def test_sweep_parity_structured(api):
     """One sequential sweep on the 8x8 shapes (Dc=16): every proposal's ratio matches the
-    oracle within 1e-5, every decision matches except at near-ties, final spins equal."""
+    oracle within RATIO_TOL_SWEEP (twice the float32 spread of this sweep), every decision
+    matches except at near-ties, final spins equal."""
     w = structured("peps_8x8", 6)
-    _sweep_parity(api, w, inputs.start_spins(6, 8, 8, 33, "random"), 77, 3, range(6), RATIO_TOL)
+    _sweep_parity(api, w, inputs.start_spins(6, 8, 8, 33, "random"), 77, 3, range(6), RATIO_TOL_SWEEP)
 
 
 def test_sweep_parity_iid_sampled(api):
