@@ -53,6 +53,27 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def rank_seeds(w, rank):
+    """One rank's share of the workload: the tensors are replicated, every rank runs its
+    own n_chains chains with its own start configurations and Metropolis key (weak
+    scaling over independent Markov chains; no data-path collective)."""
+    return {"spins": w["seed"] + 7919 * rank, "key": w["seed"] + rank}
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (timings: the job is as slow as its slowest rank)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, chains_per_rank, steps, seconds):
+    """Samples/s of the whole job: every rank's chains over the slowest rank's time."""
+    return world * chains_per_rank * steps / seconds
+
+
 class Clocks:
     """nvidia-smi samples (every 200 ms) of one GPU during the timed region."""
 
@@ -193,10 +214,11 @@ def run_ours(args):
     torch.cuda.set_device(local)
     w = inputs.workload(args.workload)
     C = w["n_chains"]
-    spins = inputs.start_spins(C, w["Ly"], w["Lx"], w["seed"] + 7919 * rank, "random")
+    seeds = rank_seeds(w, rank)
+    spins = inputs.start_spins(C, w["Ly"], w["Lx"], seeds["spins"], "random")
     prec = api.PRECISIONS[args.precision]
     ctx = api.PepsVMC(w["Ly"], w["Lx"], w["D"], w["chi"], C, w["tensors"], w["sketch"], J1=w["J1"],
-                      J2=w["J2"], seed=w["seed"] + rank, n_fit=args.n_fit, precision=prec)
+                      J2=w["J2"], seed=seeds["key"], n_fit=args.n_fit, precision=prec)
     ctx.set_spins(spins)
     delta = 1e-3
 
@@ -243,11 +265,8 @@ def run_ours(args):
     prof = ctx.get_profile()
     prof_step_ms = pe0.elapsed_time(pe1)
     ctx.set_profiling(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = world * C * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_rate(world, C, args.steps, ms / 1e3)
 
     e2e = None
     if not args.no_e2e:
@@ -267,10 +286,7 @@ def run_ours(args):
             step(args.warmup + args.steps + 1 + i, host)
         barrier()
         e2e_s = time.perf_counter() - t0
-        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * C * args.steps / float(te.item()), "unit": UNIT,
+        e2e = {"value": whole_job_rate(world, C, args.steps, max_over_ranks(e2e_s, dist, "cuda")), "unit": UNIT,
                "h2d_bytes_per_step": P * 8,
                "d2h_bytes_per_step": C * (8 + 8 + 1) + 2 * P * 8}
 
