@@ -20,6 +20,7 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmDesc d) {
   static_assert(TX * TY == 256, "256 threads per tile");
   __shared__ __align__(16) float As[BK][BM + 4];
   __shared__ __align__(16) float Bs[BK][BN + 4];
+  __shared__ long long s_on[BN];  // C offset of each tile column (the same for every row)
 
   const int b = blockIdx.y + blockIdx.z * gridDim.y;
   if (b >= d.batch) return;
@@ -34,6 +35,12 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmDesc d) {
 
   const int t = threadIdx.x;
   const int tx = t % TX, ty = t / TX;
+  for (int c = t; c < BN; c += 256) {
+    const int n = n0 + c, cn23 = d.cn2 * d.cn3;
+    s_on[c] = n < d.N ? (long long)(n / cn23) * d.sCn1 + (long long)((n / d.cn3) % d.cn2) * d.sCn2 +
+                            (long long)(n % d.cn3) * d.sCn3
+                      : 0;
+  }
   float acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -96,7 +103,7 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmDesc d) {
   float alpha = d.alpha;
   if (d.inv_scale) alpha = (float)((double)alpha / d.inv_scale[b]);
   float* __restrict__ C = d.C + (long long)b * d.bsC;
-  const int cm23 = d.cm2 * d.cm3, cn23 = d.cn2 * d.cn3;
+  const int cm23 = d.cm2 * d.cm3;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int m = m0 + ty * TM + i;
@@ -107,8 +114,7 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(const GemmDesc d) {
     for (int j = 0; j < TN; ++j) {
       const int n = n0 + tx * TN + j;
       if (n >= d.N) continue;
-      const long long on = (long long)(n / cn23) * d.sCn1 + (long long)((n / d.cn3) % d.cn2) * d.sCn2 +
-                           (long long)(n % d.cn3) * d.sCn3;
+      const long long on = s_on[tx * TN + j];
       const float v = alpha * acc[i][j];
       if (d.accumulate) C[om + on] += v; else C[om + on] = v;
     }

@@ -241,6 +241,7 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(const GemmDesc d, uns
   // stage s: A tile at s * (A_BYTES + B_BYTES), B tile right after it
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_base;
+  __shared__ long long s_on[BN];  // C offset of each tile column (the same for every row)
 
   const int b = blockIdx.y + blockIdx.z * gridDim.y;
   if (b >= d.batch) return;
@@ -252,6 +253,12 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(const GemmDesc d, uns
   if (d.sel) boff += (long long)(((d.sel[(long long)b * d.sel_stride] < 0) ? 1 : 0) ^ d.sel_xor) * d.ssB;
   const float* B = d.B + boff;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = threadIdx.x; c < BN; c += kThreads) {
+    const int n = n0 + c, cn23 = d.cn2 * d.cn3;
+    s_on[c] = n < d.N ? (long long)(n / cn23) * d.sCn1 + (long long)((n / d.cn3) % d.cn2) * d.sCn2 +
+                            (long long)(n % d.cn3) * d.sCn3
+                      : 0;
+  }
 
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])));
@@ -365,8 +372,7 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(const GemmDesc d, uns
 #pragma unroll
         for (int j = 0; j < 16; j += 4) {
           const int n = n0 + c0 + j;
-          const long long on = (long long)(n / cn23) * d.sCn1 + (long long)((n / d.cn3) % d.cn2) * d.sCn2 +
-                               (long long)(n % d.cn3) * d.sCn3;
+          const long long on = s_on[c0 + j];
           float* dst = C + om + on;
           if (vec && n + 4 <= d.N && aligned16(dst)) {
             *reinterpret_cast<float4*>(dst) =
@@ -376,8 +382,7 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(const GemmDesc d, uns
             for (int q = 0; q < 4; ++q) {
               const int nq = n + q;
               if (nq < d.N) {
-                const long long oq = (long long)(nq / cn23) * d.sCn1 + (long long)((nq / d.cn3) % d.cn2) * d.sCn2 +
-                                     (long long)(nq % d.cn3) * d.sCn3;
+                const long long oq = s_on[c0 + j + q];
                 if (d.accumulate) C[om + oq] += alpha * v[j + q]; else C[om + oq] = alpha * v[j + q];
               }
             }

@@ -57,7 +57,9 @@ def main():
     p.add_argument("--epochs", type=int, default=20)
     p.add_argument("--batch", type=int, default=256)
     p.add_argument("--lr", type=float, default=2e-3)
+    p.add_argument("--arms", default="plain,learned", help="plain, learned or both (comma separated)")
     a = p.parse_args()
+    arms = a.arms.split(",")
     w = inputs.workload(a.workload, n_chains=a.chains)
     Ly, Lx, D, chi, C = w["Ly"], w["Lx"], w["D"], w["chi"], w["n_chains"]
     if a.structured:
@@ -73,8 +75,12 @@ def main():
     base = dict(workload=a.workload, precision=a.precision, chains=C, sweeps=a.sweeps, therm=a.therm,
                 tensors="structured" if a.structured else "iid")
 
-    plain = run_arm(ctx, start, sweep0, a.sweeps, N)
-    print(json.dumps(dict(arm="plain", **base, **plain)), flush=True)
+    plain = run_arm(ctx, start, sweep0, a.sweeps, N) if "plain" in arms else None
+    if plain:
+        print(json.dumps(dict(arm="plain", **base, **plain)), flush=True)
+    if "learned" not in arms:
+        ctx.close()
+        return
 
     ctx.set_spins(start)
     ctx.set_sweep_counter(sweep0 + 10 ** 6)
@@ -93,6 +99,9 @@ def main():
     print(json.dumps(dict(arm="learned", **base, **learned, train_configs=n_train, collect_s=t1 - t0,
                           train_s=t2 - t1, loss_first_epoch=loss0, loss_last_epoch=loss,
                           learned_accept=acc)), flush=True)
+    if not plain:
+        ctx.close()
+        return
     dE = learned["E_per_site"] - plain["E_per_site"]
     sig = float(np.hypot(learned["E_err"], plain["E_err"]))
     print(json.dumps(dict(summary=True, **base, dE_per_site=dE, dE_sigma=dE / sig if sig > 0 else 0.0,
