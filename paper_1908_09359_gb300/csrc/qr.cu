@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(kQrThreads) qr_pos_kernel(const float* __restr
 }
 
 // Register-resident form for rows <= 256, cols <= 32 (every bulk shape of D <= 8,
-// Dc <= 32): thread t holds row t of the matrix and of Q in registers, so a reflector
+// Dc <= 32), in blocks of 64, 128 or 256 threads (the smallest that covers the rows):
+// thread t holds row t of the matrix and of Q in registers, so a reflector
 // costs two block reductions instead of a pass over shared memory per column.  The
 // 32-wide reductions (w = v^T A over the remaining columns) run as a transposing warp
 // butterfly (31 shuffles leave column l's warp sum in lane l), then across the eight
@@ -124,7 +125,9 @@ __device__ __forceinline__ float warp_transpose_sum32(float (&p)[kQrRegCols]) {
   return p[0];
 }
 
-// Sum over the block of p[k] for every k into tot_s[k] (shared); red: 8 x 32 floats.
+// Sum over the block (NT threads) of p[k] for every k into tot_s[k] (shared); red:
+// NT/32 x 32 floats.
+template <int NT>
 __device__ __forceinline__ void block_sum32(float (&p)[kQrRegCols], float* red, float* tot_s) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float v = warp_transpose_sum32(p);
@@ -133,17 +136,19 @@ __device__ __forceinline__ void block_sum32(float (&p)[kQrRegCols], float* red, 
   if (threadIdx.x < 32) {
     float s = 0.f;
 #pragma unroll
-    for (int w = 0; w < kQrThreads / 32; ++w) s += red[w * 32 + threadIdx.x];
+    for (int w = 0; w < NT / 32; ++w) s += red[w * 32 + threadIdx.x];
     tot_s[threadIdx.x] = s;
   }
   __syncthreads();
 }
 
 // Y and Q may be the same array (in-place QR): every row is read before any is written.
-__global__ void __launch_bounds__(kQrThreads) qr_pos_reg_kernel(const float* Y, long long bsY, long long yrs,
+// NT threads (64, 128 or 256) hold up to NT rows.
+template <int NT>
+__global__ void __launch_bounds__(NT) qr_pos_reg_kernel(const float* Y, long long bsY, long long yrs,
                                                                 long long ycs, float* Q, long long bsQ,
                                                                 long long qrs, long long qcs, int R, int C) {
-  __shared__ float red[kQrThreads];
+  __shared__ float red[NT];
   __shared__ float tot[kQrRegCols];
   __shared__ float beta[kQrRegCols];
   __shared__ int flip[kQrRegCols];
@@ -169,7 +174,7 @@ __global__ void __launch_bounds__(kQrThreads) qr_pos_reg_kernel(const float* Y, 
     if (t == 0) {
       float n2 = 0.f;
 #pragma unroll
-      for (int w = 0; w < kQrThreads / 32; ++w) n2 += red[w];
+      for (int w = 0; w < NT / 32; ++w) n2 += red[w];
       nrm = sqrtf(n2);
     }
     __syncthreads();
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(kQrThreads) qr_pos_reg_kernel(const float* Y, 
     const float v = (t >= j) ? a[j] : 0.f;
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k) p[k] = (k > j) ? v * a[k] : 0.f;
-    block_sum32(p, red, tot);
+    block_sum32<NT>(p, red, tot);
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k)
       if (k > j) a[k] = fmaf(-bj * tot[k], v, a[k]);
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(kQrThreads) qr_pos_reg_kernel(const float* Y, 
     const float v = (t >= j) ? a[j] : 0.f;
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k) p[k] = (k >= j) ? v * q[k] : 0.f;
-    block_sum32(p, red, tot);
+    block_sum32<NT>(p, red, tot);
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k)
       if (k >= j) q[k] = fmaf(-bj * tot[k], v, q[k]);
@@ -221,8 +226,13 @@ cudaError_t qr_pos_batched(const float* Y, long long bsY, long long yrs, long lo
                            cudaStream_t st) {
   if (g_dry_run || batch <= 0) return cudaSuccess;
   if (cols > kQrMaxCols || rows < cols || cols <= 0) return cudaErrorInvalidValue;
-  if (rows <= kQrThreads && cols <= kQrRegCols) {
-    qr_pos_reg_kernel<<<batch, kQrThreads, 0, st>>>(Y, bsY, yrs, ycs, Q, bsQ, qrs, qcs, rows, cols);
+  if (rows <= 256 && cols <= kQrRegCols) {
+    if (rows <= 64)
+      qr_pos_reg_kernel<64><<<batch, 64, 0, st>>>(Y, bsY, yrs, ycs, Q, bsQ, qrs, qcs, rows, cols);
+    else if (rows <= 128)
+      qr_pos_reg_kernel<128><<<batch, 128, 0, st>>>(Y, bsY, yrs, ycs, Q, bsQ, qrs, qcs, rows, cols);
+    else
+      qr_pos_reg_kernel<256><<<batch, 256, 0, st>>>(Y, bsY, yrs, ycs, Q, bsQ, qrs, qcs, rows, cols);
     return cudaGetLastError();
   }
   const size_t smem = (size_t)2 * rows * cols * sizeof(float);
