@@ -138,7 +138,8 @@ def test_amplitude_parity_finite_dc(api, row):
 
 # ------------------------------------------------------------ measurement (a6, a7, a8)
 
-@pytest.mark.parametrize("case", ["4x4_exact", "8x8_structured", "6x6_j1j2_structured", "8x8_iid_sampled"])
+@pytest.mark.parametrize("case", ["4x4_exact", "8x8_structured", "6x6_j1j2_structured", "6x6_d4_dc24_structured",
+                                  "8x8_iid_sampled"])
 def test_measure_parity(api, case):
     eloc_tol, grad_tol = ELOC_TOL, GRAD_TOL
     n_fit = 3
@@ -151,6 +152,10 @@ def test_measure_parity(api, case):
     elif case == "6x6_j1j2_structured":
         w = small_workload(6, 6, 3, 9, J2=0.5, seed=4, decay=DECAY)
         sp = inputs.start_spins(4, 6, 6, 21, "random")
+    elif case == "6x6_d4_dc24_structured":
+        # D Dc = 96 rows per fitted site: the 128-thread form of the register QR
+        w = small_workload(6, 6, 4, 24, seed=6, decay=DECAY)
+        sp = inputs.start_spins(3, 6, 6, 23, "random")
     else:
         w = inputs.workload("peps_8x8", n_chains=8)
         sp = golden.load("peps_8x8")
