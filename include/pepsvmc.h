@@ -253,7 +253,9 @@ int pepsvmc_get_profile_shapes(pepsvmc_ctx* ctx, char* buf, int64_t len);
 int pepsvmc_set_autotune(pepsvmc_ctx* ctx, int32_t on);
 
 /* Fix the kernel of every contraction of this context (kernel-level profiling and
- * tests; the automatic choice computes the same products).  kind 0: automatic (the
+ * tests; the automatic choice computes the same products).  The paper has no
+ * counterpart: this selects among this library's implementations of the products of
+ * App. B and App. C.  kind 0: automatic (the
  * autotuner, or the size heuristic with autotuning off); 1: FP32 CUDA-core kernel
  * with tile-table entry `tile` (0..5); 2: tcgen05 kernel with N tile `tile` (32, 64,
  * 128, 256), mixed precisions only.  Drops a captured step graph.
