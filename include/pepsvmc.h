@@ -222,6 +222,15 @@ int64_t pepsvmc_proposal_dataset_size(const pepsvmc_ctx* ctx);
  * (float64 [n][2][Ly][Lx], same channel layout as the logits).                   */
 int pepsvmc_proposal_load(pepsvmc_ctx* ctx, const int8_t* spins, const double* rho, int64_t n);
 int pepsvmc_proposal_train(pepsvmc_ctx* ctx, int32_t epochs, int32_t batch, double lr, double* loss_out);
+/* Train on given configurations (host int8 [n][Ly][Lx], +-1): each is measured with
+ * this context's environments (batches of n_chains; its NN ratios rho give the targets
+ * log min(1, rho^2)), the training set is replaced by them, then `epochs` Adam epochs
+ * in minibatches of min(256, n) run; final_loss_out (nullable) gets the last epoch's
+ * mean loss.  The chains' own configurations are restored afterwards (their last
+ * measurement is discarded).  Errors: EINVAL (bad sizes, spins not +-1, lr <= 0),
+ * ESTATE (no network), ENOMEM.                                                      */
+int pepsvmc_train_proposal(pepsvmc_ctx* ctx, const int8_t* configs, int64_t n, int32_t epochs, double lr,
+                           double* final_loss_out);
 int pepsvmc_set_proposal(pepsvmc_ctx* ctx, int32_t mode);
 int pepsvmc_learned_sweep(pepsvmc_ctx* ctx, int32_t n_sweeps, double* accept_rate_out);
 int pepsvmc_get_learned_trace(pepsvmc_ctx* ctx, double* rho, double* dlq, int8_t* decision);

@@ -32,7 +32,7 @@ SYMBOLS = [
     "pepsvmc_set_contraction_kernel",
     "pepsvmc_set_graphs", "pepsvmc_set_proposal_params", "pepsvmc_get_proposal_params",
     "pepsvmc_proposal_logits", "pepsvmc_proposal_collect", "pepsvmc_proposal_dataset_size", "pepsvmc_proposal_load",
-    "pepsvmc_proposal_train", "pepsvmc_set_proposal", "pepsvmc_learned_sweep", "pepsvmc_get_learned_trace",
+    "pepsvmc_proposal_train", "pepsvmc_train_proposal", "pepsvmc_set_proposal", "pepsvmc_learned_sweep", "pepsvmc_get_learned_trace",
 ]
 
 
@@ -100,6 +100,7 @@ def load(path: str | None = None):
         "pepsvmc_proposal_dataset_size": (I64, [P]),
         "pepsvmc_proposal_load": (C.c_int, [P, I8, D, I64]),
         "pepsvmc_proposal_train": (C.c_int, [P, I32, I32, C.c_double, D]),
+        "pepsvmc_train_proposal": (C.c_int, [P, C.POINTER(C.c_int8), C.c_int64, I32, C.c_double, C.POINTER(C.c_double)]),
         "pepsvmc_set_proposal": (C.c_int, [P, I32]),
         "pepsvmc_learned_sweep": (C.c_int, [P, I32, D]),
         "pepsvmc_get_learned_trace": (C.c_int, [P, D, D, I8]),

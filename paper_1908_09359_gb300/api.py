@@ -203,6 +203,9 @@ class PepsVMC:
         self._check(self.lib.pepsvmc_proposal_collect(self.ctx, int(n_sweeps)))
         return int(self.lib.pepsvmc_proposal_dataset_size(self.ctx))
 
+    def proposal_dataset_size(self):
+        return int(self.lib.pepsvmc_proposal_dataset_size(self.ctx))
+
     def proposal_load(self, spins, rho):
         s = np.ascontiguousarray(spins, dtype=np.int8)
         r = np.ascontiguousarray(rho, dtype=np.float64)
@@ -211,6 +214,15 @@ class PepsVMC:
     def proposal_train(self, epochs, batch, lr):
         loss = C.c_double()
         self._check(self.lib.pepsvmc_proposal_train(self.ctx, int(epochs), int(batch), float(lr), C.byref(loss)))
+        return loss.value
+
+    def train_proposal(self, configs, epochs, lr):
+        """Measure the given +-1 configurations (n, Ly, Lx), train on them, return the
+        last epoch's mean loss."""
+        c = np.ascontiguousarray(configs, dtype=np.int8).reshape(-1, self.Ly, self.Lx)
+        loss = C.c_double()
+        self._check(self.lib.pepsvmc_train_proposal(self.ctx, _i8(c), int(len(c)), int(epochs), float(lr),
+                                                     C.byref(loss)))
         return loss.value
 
     def set_proposal(self, mode):

@@ -1117,6 +1117,7 @@ struct pepsvmc_ctx {
   int8_t* ds_spins = nullptr;
   float* ds_rho = nullptr;
   long long ds_cap = 0, ds_n = 0;
+  int8_t* spins_saved = nullptr;  // chain spins kept aside while pepsvmc_train_proposal measures
   float *tr_h1 = nullptr, *tr_h2 = nullptr, *tr_out = nullptr, *tr_d1 = nullptr, *tr_d2 = nullptr;
   int tr_batch = 0;
 
@@ -1642,6 +1643,56 @@ int pepsvmc_proposal_collect(pepsvmc_ctx* x, int32_t n_sweeps) {
 }
 
 int64_t pepsvmc_proposal_dataset_size(const pepsvmc_ctx* x) { return x ? x->ds_n : 0; }
+
+int pepsvmc_train_proposal(pepsvmc_ctx* x, const int8_t* configs, int64_t n, int32_t epochs, double lr,
+                           double* final_loss_out) {
+  if (!x || !configs || n < 1 || epochs < 1 || !(lr > 0.0)) return PEPSVMC_EINVAL;
+  if (!x->net_ready) return x->fail(PEPSVMC_ESTATE, "no proposal network: call pepsvmc_set_proposal_params");
+  const long long N = (long long)x->Ly * x->Lx;
+  for (long long i = 0; i < n * N; ++i)
+    if (configs[i] != 1 && configs[i] != -1) return x->fail(PEPSVMC_EINVAL, "configurations must be +1 or -1");
+  cudaError_t e = cudaSuccess;
+  // the training set is replaced; a measurement exports the ratios of all C chains, so
+  // the last (partial) batch needs room for C entries
+  const long long need = n + x->C;
+  if (need > x->ds_cap) {
+    int8_t* s2 = nullptr;
+    float* r2 = nullptr;
+    if ((e = x->alloc(&s2, (size_t)need * N)) || (e = x->alloc(&r2, (size_t)need * 2 * N)))
+      return x->fail(PEPSVMC_ENOMEM, "training set allocation failed");
+    x->ds_spins = s2;
+    x->ds_rho = r2;
+    x->ds_cap = need;
+  }
+  if (!x->spins_saved && (e = x->alloc(&x->spins_saved, (size_t)x->C * N)))
+    return x->fail(PEPSVMC_ENOMEM, "allocation failed");
+  if ((e = x->cp(x->spins_saved, x->spins, (size_t)x->C * N, cudaMemcpyDeviceToDevice))) return x->fail_cuda(e);
+  x->ds_n = 0;
+  std::vector<int8_t> batch((size_t)x->C * N);
+  for (long long b0 = 0; b0 < n; b0 += x->C) {
+    const long long cnt = std::min<long long>(x->C, n - b0);
+    for (long long c = 0; c < x->C; ++c)
+      memcpy(&batch[(size_t)(c * N)], configs + (b0 + (c < cnt ? c : 0)) * N, (size_t)N);
+    if ((e = x->cps(x->spins, batch.data(), batch.size(), cudaMemcpyHostToDevice))) return x->fail_cuda(e);
+    x->top_valid = false;
+    x->rho_export = x->ds_rho + x->ds_n * 2 * N;
+    e = x->measure_dev();
+    x->rho_export = nullptr;
+    if (e || (e = x->cp(x->ds_spins + x->ds_n * N, x->spins, (size_t)cnt * N, cudaMemcpyDeviceToDevice)))
+      return x->fail_cuda(e);
+    x->ds_n += cnt;
+    const int rc = x->check_status();
+    if (rc) return rc;
+  }
+  if ((e = x->cp(x->spins, x->spins_saved, (size_t)x->C * N, cudaMemcpyDeviceToDevice))) return x->fail_cuda(e);
+  x->top_valid = false;
+  x->have_measure = false;
+  e = x->train_epochs(epochs, (int)std::min<long long>(256, x->ds_n), (float)lr, final_loss_out);
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  x->drop_graph();
+  x->eager_steps = 0;
+  return x->check_status();
+}
 
 int pepsvmc_proposal_load(pepsvmc_ctx* x, const int8_t* spins, const double* rho, int64_t n) {
   if (!x || !spins || !rho || n < 1) return PEPSVMC_EINVAL;

@@ -128,3 +128,27 @@ def test_training_on_sampled_configurations_lowers_the_loss(api):
     r = ctx.energy_and_grad(2)
     assert np.all(np.isfinite(r["eloc"]))
     ctx.close()
+
+
+def test_train_proposal_on_given_configurations(api):
+    """pepsvmc_train_proposal measures the caller's configurations in batches of the
+    context's chains (the last batch partial), trains on exactly those, and leaves the
+    chains' own configurations in place."""
+    n_chains, n = 64, 150
+    w = structured_8x8(n_chains)
+    ctx = api.PepsVMC(8, 8, 4, 16, n_chains, w["tensors"], w["sketch"], seed=2)
+    own = inputs.start_spins(n_chains, 8, 8, 4, "random")
+    ctx.set_spins(own)
+    ctx.set_proposal_params(inputs.proposal_params(1))
+    configs = inputs.start_spins(n, 8, 8, 9, "random")
+    first = ctx.train_proposal(configs, 1, 2e-3)
+    assert ctx.proposal_dataset_size() == n
+    assert np.array_equal(ctx.get_spins(), own)
+    last = ctx.train_proposal(configs, 12, 2e-3)
+    assert np.isfinite(first) and last < first, (first, last)
+    with pytest.raises(Exception):
+        ctx.train_proposal(np.zeros((2, 8, 8)), 1, 2e-3)
+    ctx.set_proposal(1)
+    r = ctx.energy_and_grad(1)
+    assert np.all(np.isfinite(r["eloc"]))
+    ctx.close()
