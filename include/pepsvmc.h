@@ -255,10 +255,11 @@ int pepsvmc_get_profile_shapes(pepsvmc_ctx* ctx, char* buf, int64_t len);
 
 /* Autotuner (on by default): the first launch of every contraction shape times each
  * candidate kernel (six FP32 tile shapes; in the tensor-core modes also the TC tile
- * widths 32/64/128/256) with CUDA events and keeps the fastest for this context.
+ * widths 32/64/128/256, and in split BF16 the two-stage form at 32/64 for products
+ * with K > 64) with CUDA events and keeps the fastest for this context.
  * pepsvmc_set_autotune(ctx, 0) turns it off and forgets the choices (fixed
  * heuristics then); pepsvmc_get_tuning writes the choices as JSON text:
- * [{"shape": "...", "choice": "f32_cfg3" | "tc_bn64", "candidate_ms": [...]}, ...]. */
+ * [{"shape": "...", "choice": "f32_cfg3" | "tc_bn64" | "tc2_bn32", "candidate_ms": [...]}, ...]. */
 int pepsvmc_set_autotune(pepsvmc_ctx* ctx, int32_t on);
 
 /* Fix the kernel of every contraction of this context (kernel-level profiling and
@@ -267,8 +268,9 @@ int pepsvmc_set_autotune(pepsvmc_ctx* ctx, int32_t on);
  * App. B and App. C.  kind 0: automatic (the
  * autotuner, or the size heuristic with autotuning off); 1: FP32 CUDA-core kernel
  * with tile-table entry `tile` (0..5); 2: tcgen05 kernel with N tile `tile` (32, 64,
- * 128, 256), mixed precisions only.  Drops a captured step graph.
- * Errors: EINVAL (unknown kind or tile, or kind 2 at FP32).                        */
+ * 128, 256), mixed precisions only; 3: its split-BF16 form with two shared-memory
+ * stages, N tile 32 or 64, PEPSVMC_MIXED_BF16X3 only.  Drops a captured step graph.
+ * Errors: EINVAL (unknown kind or tile, or a kind the precision lacks).            */
 int pepsvmc_set_contraction_kernel(pepsvmc_ctx* ctx, int32_t kind, int32_t tile);
 
 /* CUDA graphs (on by default): pepsvmc_energy_and_grad runs its first sample step

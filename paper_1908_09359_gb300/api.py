@@ -243,8 +243,9 @@ class PepsVMC:
         self._check(self.lib.pepsvmc_set_graphs(self.ctx, 1 if on else 0))
 
     def set_contraction_kernel(self, kind, tile=0):
-        """kind: "auto", "f32" (tile 0..5) or "tc" (N tile 32, 64, 128, 256)."""
-        k = {"auto": 0, "f32": 1, "tc": 2}[kind]
+        """kind: "auto", "f32" (tile 0..5), "tc" (N tile 32, 64, 128, 256) or "tc2" (split
+        BF16 with two shared-memory stages, N tile 32 or 64)."""
+        k = {"auto": 0, "f32": 1, "tc": 2, "tc2": 3}[kind]
         self._check(self.lib.pepsvmc_set_contraction_kernel(self.ctx, k, int(tile)))
 
     def set_autotune(self, on=True):

@@ -42,7 +42,8 @@ int gemm_f32_pick(const GemmDesc& d);
 
 // Same contraction on the tcgen05 tensor cores with FP32 accumulation in tensor memory.
 // mode 2: operands rounded to BF16 (kind::f16); 3: split BF16, x = hi + lo, three MMAs
-// per step; 4: operands rounded to TF32 (kind::tf32).  Device waits are bounded; on
+// per step; 4: operands rounded to TF32 (kind::tf32); 6: mode 3 with two shared-memory
+// stages (bn 32 or 64).  Device waits are bounded; on
 // expiry ST_TIMEOUT is set in *status.  bn: N tile (32, 64, 128, 256; 0 = smallest >= N).
 cudaError_t gemm_tc(const GemmDesc& d, int mode, int bn, unsigned* status, cudaStream_t st);
 

@@ -228,13 +228,15 @@ __device__ __forceinline__ void load_tile(uint8_t* tile, const float* base, long
 
 // X3: split BF16 operands, x = hi + lo, and D += A_hi B_hi + A_hi B_lo + A_lo B_hi (the
 // lo*lo term, ~2^-18 relative, is dropped): close to FP32 accuracy at BF16 cost.  One
-// shared-memory stage holds [A_hi | B_hi | A_lo | B_lo]; plain modes double-buffer.
-template <int EB, int BN, bool X3>
+// shared-memory stage holds [A_hi | B_hi | A_lo | B_lo]; plain modes double-buffer, and
+// so does the split mode with DB (twice the shared memory, so fewer resident blocks:
+// a candidate for long-K products, where loading stage k+1 then overlaps the MMAs of k).
+template <int EB, int BN, bool X3, bool DB = false>
 __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(const GemmDesc d, unsigned* status) {
   constexpr int BK = kKBytes / EB;   // K elements per stage
   constexpr int MMA_K = 32 / EB;     // K elements per tcgen05.mma (32 bytes)
   constexpr int A_BYTES = kBM * kKBytes, B_BYTES = BN * kKBytes;
-  constexpr int STAGES = X3 ? 1 : 2;
+  constexpr int STAGES = (X3 && !DB) ? 1 : 2;
   constexpr int STAGE_BYTES = (X3 ? 2 : 1) * (A_BYTES + B_BYTES);
   constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -396,17 +398,19 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(const GemmDesc d, uns
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
-template <int EB, int BN, bool X3>
+template <int EB, int BN, bool X3, bool DB = false>
 cudaError_t launch(const GemmDesc& d, unsigned* status, cudaStream_t st) {
-  constexpr int smem = 2 * (kBM + BN) * kKBytes;  // two plain stages, or one split stage
+  // two plain stages, one split stage, or two split stages (DB)
+  constexpr int smem = (DB ? 4 : 2) * (kBM + BN) * kKBytes;
   static bool configured = false;
   if (!configured) {
-    PV_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<EB, BN, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PV_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<EB, BN, X3, DB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem));
     configured = true;
   }
   const int tiles = ((d.M + kBM - 1) / kBM) * ((d.N + BN - 1) / BN);
   dim3 grid(tiles, d.batch < 65535 ? d.batch : 65535, (d.batch + 65534) / 65535);
-  gemm_tc_kernel<EB, BN, X3><<<grid, kThreads, smem, st>>>(d, status);
+  gemm_tc_kernel<EB, BN, X3, DB><<<grid, kThreads, smem, st>>>(d, status);
   return cudaGetLastError();
 }
 
@@ -425,12 +429,19 @@ cudaError_t launch_bn(const GemmDesc& d, int bn, unsigned* status, cudaStream_t 
 
 // Shared memory per CTA is 2 x (128 + BN) rows x 128 B, i.e. 40/48/64/96 KB for
 // BN = 32/64/128/256, so at most 5/4/3/2 CTAs share an SM and their tensor memory
-// (BN columns each) never exceeds the SM's 512 columns: allocation never waits.
-// mode: 2 = BF16, 3 = split BF16 (hi + lo), 4 = TF32.
+// (BN columns each) never exceeds the SM's 512 columns: allocation never waits.  The
+// double-buffered split mode (BN = 32/64 only) takes 80/96 KB: at most 2 CTAs per SM.
+// mode: 2 = BF16, 3 = split BF16 (hi + lo), 4 = TF32, 6 = split BF16 double-buffered.
 // bn: tile width 32/64/128/256, or 0 for the smallest that covers N.
 cudaError_t gemm_tc(const GemmDesc& d, int mode, int bn, unsigned* status, cudaStream_t st) {
   if (g_dry_run || d.M <= 0 || d.N <= 0 || d.batch <= 0) return cudaSuccess;
   if (bn != 0 && bn != 32 && bn != 64 && bn != 128 && bn != 256) return cudaErrorInvalidValue;
+  if (mode == 6) {
+    if (bn == 0) bn = d.N <= 32 ? 32 : 64;
+    if (bn == 32) return launch<2, 32, true, true>(d, status, st);
+    if (bn == 64) return launch<2, 64, true, true>(d, status, st);
+    return cudaErrorInvalidValue;
+  }
   if (mode == 2) return launch_bn<2, false>(d, bn, status, st);
   if (mode == 3) return launch_bn<2, true>(d, bn, status, st);
   return launch_bn<4, false>(d, bn, status, st);

@@ -330,7 +330,7 @@ struct pepsvmc_ctx {
   // Candidates compute the same product, so the timing runs are harmless.
   bool autotune = true;
   bool capturing = false;
-  std::map<std::string, int> tuned;               // choice: f32 config, or 100 + TC tile width
+  std::map<std::string, int> tuned;  // choice: f32 config, 100 + TC tile width, 1000 + two-stage split tile width
   std::map<std::string, std::vector<float>> tune_ms;
 
   static std::string tune_key(const GemmDesc& g) {
@@ -341,6 +341,7 @@ struct pepsvmc_ctx {
     return k;
   }
   cudaError_t run_choice(const GemmDesc& g, int choice) {
+    if (choice >= 1000) return gemm_tc(g, 6, choice - 1000, status, st);  // split BF16, two stages
     if (choice >= 100) return gemm_tc(g, tc_mode(), choice - 100, status, st);
     return gemm_f32(g, choice, st);
   }
@@ -348,8 +349,11 @@ struct pepsvmc_ctx {
     std::vector<int> cand;
     for (int c = 0; c < gemm_f32_num_configs(); ++c) cand.push_back(c);
     if (tc_mode() && g.K >= 8)
-      for (int bn : {32, 64, 128, 256})
+      for (int bn : {32, 64, 128, 256}) {
         if (bn / 2 < g.N || bn == 32) cand.push_back(100 + bn);
+        // the double-buffered split form, for products with more than one K stage
+        if (tc_mode() == 3 && bn <= 64 && g.K > 64 && (bn / 2 < g.N || bn == 32)) cand.push_back(1000 + bn);
+      }
     cudaEvent_t e0 = ev(), e1 = ev();
     int best = -1;
     float best_ms = 0.f;
@@ -1785,6 +1789,7 @@ int pepsvmc_set_contraction_kernel(pepsvmc_ctx* x, int32_t kind, int32_t tile) {
   int choice = -1;
   if (kind == 1 && tile >= 0 && tile < gemm_f32_num_configs()) choice = tile;
   if (kind == 2 && x->tc_mode() && (tile == 32 || tile == 64 || tile == 128 || tile == 256)) choice = 100 + tile;
+  if (kind == 3 && x->tc_mode() == 3 && (tile == 32 || tile == 64)) choice = 1000 + tile;
   if (kind != 0 && choice < 0) return x->fail(PEPSVMC_EINVAL, "no such contraction kernel for this precision");
   x->forced = choice;
   x->drop_graph();
@@ -1801,7 +1806,8 @@ int pepsvmc_get_tuning(pepsvmc_ctx* x, char* buf, int64_t len) {
     for (float t : x->tune_ms[kv.first]) times += (times.empty() ? "" : ",") + std::to_string(t);
     char row[512];
     snprintf(row, sizeof(row), "%s{\"shape\":\"%s\",\"choice\":\"%s%d\",\"candidate_ms\":[%s]}",
-             js.size() > 1 ? "," : "", kv.first.c_str(), c >= 100 ? "tc_bn" : "f32_cfg", c >= 100 ? c - 100 : c,
+             js.size() > 1 ? "," : "", kv.first.c_str(), c >= 1000 ? "tc2_bn" : c >= 100 ? "tc_bn" : "f32_cfg",
+             c >= 1000 ? c - 1000 : c >= 100 ? c - 100 : c,
              times.c_str());
     js += row;
   }

@@ -53,18 +53,19 @@ def test_env3_tensor_cores_match_oracle(torch_mod, precision, dims):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", [1, 2, 3])
-@pytest.mark.parametrize("bn", [32, 64, 128, 256])
-def test_env3_every_tile_width_matches_oracle(torch_mod, precision, bn):
-    """Each tcgen05 tile width fixed for all three products of the step (the autotuner
-    would otherwise pick per shape), at the 24x24 bulk shapes with 300 chains."""
+@pytest.mark.parametrize("precision,kind,bn", [(p, "tc", b) for p in (1, 2, 3) for b in (32, 64, 128, 256)]
+                         + [(3, "tc2", 32), (3, "tc2", 64)])
+def test_env3_every_tile_width_matches_oracle(torch_mod, precision, kind, bn):
+    """Each tcgen05 kernel form and tile width fixed for all three products of the step
+    (the autotuner would otherwise pick per shape), at the 24x24 bulk shapes with 300
+    chains; "tc2" is the split-BF16 form with two shared-memory stages."""
     torch = torch_mod
     from paper_1908_09359_gb300 import api, inputs
     dims = (300, 32, 32, 32, 32, 8, 8, 8, 8)
     n, cT, cB, cT2, cB2, Dl, Dr, Du, Dd = dims
     ctx = api.PepsVMC(8, 8, 8, 32, n, inputs.peps_tensors(8, 8, 8, 1), inputs.sketch(8, 32, 8, 1),
                       seed=1, precision=precision)
-    ctx.set_contraction_kernel("tc", bn)
+    ctx.set_contraction_kernel(kind, bn)
     rng = np.random.default_rng(bn + precision)
     f32 = lambda *s: rng.standard_normal(s).astype(np.float32)  # noqa: E731
     E, T, A, B = f32(n, cT, Dl, cB), f32(n, cT, Du, cT2), f32(2, Dl, Dr, Du, Dd), f32(n, cB, Dd, cB2)
