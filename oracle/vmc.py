@@ -27,7 +27,7 @@ Readings of points the paper leaves open (each is listed in the design notes):
   to bottom, through the transposed lattice), then horizontal bonds (rows top to
   bottom, bonds left to right).  Only antiparallel pairs are proposed.
 * Ratios on the vertical bonds and on the J2 diagonals in E_loc use four-line
-  environments of a row pair (App. C, "similarly computed").
+  environments of a row pair (App. C works out only the horizontal case).
 """
 from __future__ import annotations
 
