@@ -58,16 +58,21 @@ typedef struct {
   double J1, J2;        /* NN and NNN couplings; J2 = 0 is Heisenberg      */
   uint64_t seed;        /* Philox key for Metropolis and sign-SGD uniforms */
   int32_t precision;    /* PEPSVMC_FP32 or one of the PEPSVMC_MIXED_* modes  */
-  int32_t reserved[7];  /* must be zero                                    */
+  int32_t chi_measure;  /* Dc of the measurement (E_loc, Psi, G), 0..64;    */
+                        /* 0 = chi.  chi is then the sampler's Dc (Sec. II A */
+                        /* and App. D use a smaller cutoff for sampling)    */
+  int32_t reserved[6];  /* must be zero                                    */
 } pepsvmc_config;
 
 /* Create a context (on failure *out may still receive a context that holds the
  * error text; pass it to pepsvmc_destroy).  Boundary-MPS truncation (App. B) is the variational fit
  * of ||M|U> - |U'>||^2 by n_fit one-site half-sweeps; its starting guess is the
- * random MPS ``sketch``.
+ * random MPS ``sketch``.  The sampler truncates to chi, the measurement to
+ * chi_measure (when nonzero; pepsvmc_amplitude uses chi).
  *   tensors: host, packed layout above, float64, copied.
- *   sketch:  host float64 array [max(Ly,Lx)][chi][D][chi] of iid N(0,1)
- *            entries, copied.
+ *   sketch:  host float64 array [max(Ly,Lx)][X][D][X] of iid N(0,1) entries,
+ *            X = max(chi, chi_measure), copied; a fit with cutoff c uses the
+ *            leading [c][D][c] corner of each site.
  *   stream:  a cudaStream_t (NULL = the legacy default stream).
  * All chains start in the Neel configuration; use pepsvmc_set_spins to change.
  * Errors: EINVAL (bad config), ENOMEM, ECUDA.                               */

@@ -40,7 +40,7 @@ class Config(C.Structure):
     _fields_ = [("Ly", C.c_int32), ("Lx", C.c_int32), ("D", C.c_int32), ("chi", C.c_int32),
                 ("n_chains", C.c_int32), ("n_fit", C.c_int32), ("J1", C.c_double),
                 ("J2", C.c_double), ("seed", C.c_uint64), ("precision", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("chi_measure", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class PepsvmcError(RuntimeError):

@@ -32,11 +32,12 @@ class PepsVMC:
     """
 
     def __init__(self, Ly, Lx, D, chi, n_chains, tensors, sketch, J1=1.0, J2=0.0, seed=0, n_fit=3,
-                 precision=FP32, stream=None):
+                 precision=FP32, stream=None, chi_measure=0):
         self.lib = _lib.load()
         cfg = _lib.Config()
         cfg.Ly, cfg.Lx, cfg.D, cfg.chi, cfg.n_chains, cfg.n_fit = Ly, Lx, D, chi, n_chains, n_fit
         cfg.J1, cfg.J2, cfg.seed, cfg.precision = float(J1), float(J2), int(seed), int(precision)
+        cfg.chi_measure = int(chi_measure)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -44,8 +45,9 @@ class PepsVMC:
         self.n_chains, self.Ly, self.Lx = n_chains, Ly, Lx
         t = np.ascontiguousarray(tensors, dtype=np.float64)
         s = np.ascontiguousarray(sketch, dtype=np.float64)
-        if s.shape != (max(Ly, Lx), chi, D, chi):
-            raise ValueError(f"sketch must have shape {(max(Ly, Lx), chi, D, chi)}")
+        X = max(chi, chi_measure)
+        if s.shape != (max(Ly, Lx), X, D, X):
+            raise ValueError(f"sketch must have shape {(max(Ly, Lx), X, D, X)}")
         self.ctx = C.c_void_p()
         rc = self.lib.pepsvmc_init(C.byref(cfg), _dp(t), _dp(s), C.c_void_p(stream), C.byref(self.ctx))
         if rc != 0:

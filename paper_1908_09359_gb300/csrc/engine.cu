@@ -90,6 +90,9 @@ struct pepsvmc_ctx {
   cudaStream_t st = nullptr;
   std::string err;
   int C = 0, Ly = 0, Lx = 0, D = 0, chi = 0, nfit = 1, Lmax = 0;
+  // chi: the cutoff the fit uses now; the sampler's (chi_s) except inside a measurement
+  // with its own cutoff (chi_m); chi_x = max of both sizes the buffers and the sketch
+  int chi_s = 0, chi_m = 0, chi_x = 0;
   long long P = 0, Ph = 0, S = 0, S4 = 0, SI = 0;
   Orient O[4];
   std::vector<long long> site_off, site_half_off;  // original sites
@@ -735,7 +738,7 @@ struct pepsvmc_ctx {
       for (int a = 0; a < vb[m]; ++a)
         for (int d = 0; d < p[m]; ++d)
           for (int b = 0; b < vb[m + 1]; ++b)
-            host.push_back((float)sketch_host[(((size_t)m * chi + a) * D + d) * chi + b]);
+            host.push_back((float)sketch_host[(((size_t)m * chi_x + a) * D + d) * chi_x + b]);
     }
     if ((e = alloc(&sk.dev, host.size())) != cudaSuccess) return sketches[key];
     if ((e = cp(sk.dev, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -979,9 +982,21 @@ struct pepsvmc_ctx {
 
   // ------------------------------------------------ measurement (Eqs. (3)-(7), App. C)
   cudaError_t measure_dev() {
+    if (chi_m != chi_s) {
+      // the measurement's own cutoff: fresh top environments at chi_m; the sampler's
+      // are no longer in st_top afterwards
+      chi = chi_m;
+      top_valid = false;
+      const cudaError_t e = measure_at_cutoff();
+      chi = chi_s;
+      return e;
+    }
+    return measure_at_cutoff();
+  }
+  cudaError_t measure_at_cutoff() {
     if (!top_valid) {
       PV_CUDA(top_down_all(0, st_top));
-      top_valid = true;
+      top_valid = chi == chi_s;
     }
     PV_CUDA(top_down_all(1, st_bot));
     ++launches;
@@ -1308,7 +1323,9 @@ int validate(const pepsvmc_config* c, std::string& why) {
   if ((c->Ly * c->Lx) % 2) { why = "Ly*Lx must be even (S^z = 0 sector)"; return PEPSVMC_EINVAL; }
   if (c->D < 1 || c->D > 16) { why = "D must be in 1..16"; return PEPSVMC_EINVAL; }
   if (c->chi < 1 || c->chi > 64) { why = "chi must be in 1..64"; return PEPSVMC_EINVAL; }
-  if ((long long)c->chi * c->chi * c->D * 2 * 4 > 200 * 1024) { why = "chi*chi*D too large for the QR kernel"; return PEPSVMC_EINVAL; }
+  if (c->chi_measure < 0 || c->chi_measure > 64) { why = "chi_measure must be in 0..64"; return PEPSVMC_EINVAL; }
+  const long long cx = std::max(c->chi, c->chi_measure);
+  if (cx * cx * c->D * 2 * 4 > 200 * 1024) { why = "chi*chi*D too large for the QR kernel"; return PEPSVMC_EINVAL; }
   if (c->n_chains < 1 || c->n_chains > (1 << 20)) { why = "n_chains must be >= 1"; return PEPSVMC_EINVAL; }
   if (c->n_fit < 1 || c->n_fit % 2 == 0) { why = "n_fit must be odd and >= 1"; return PEPSVMC_EINVAL; }
   if (c->precision != PEPSVMC_FP32 && c->precision != PEPSVMC_MIXED_BF16 && c->precision != PEPSVMC_MIXED_TF32 &&
@@ -1316,7 +1333,7 @@ int validate(const pepsvmc_config* c, std::string& why) {
     why = "unknown precision";
     return PEPSVMC_EINVAL;
   }
-  for (int i = 0; i < 7; ++i)
+  for (int i = 0; i < 6; ++i)
     if (c->reserved[i]) { why = "reserved fields must be zero"; return PEPSVMC_EINVAL; }
   return PEPSVMC_OK;
 }
@@ -1328,9 +1345,10 @@ int setup(pepsvmc_ctx* x, const double* tensors, const double* sketch) {
   x->O[2] = {Lx, Ly, true, false};
   x->O[3] = {Lx, Ly, true, true};
   x->Lmax = std::max(Ly, Lx);
-  x->S = (long long)x->chi * D * x->chi;
-  x->S4 = (long long)x->chi * D * D * x->chi;
-  x->SI = std::max((long long)D * D * D * x->chi * x->chi, std::max(x->S, (long long)D * D * x->chi * x->chi));
+  const long long X = x->chi_x;
+  x->S = X * D * X;
+  x->S4 = X * D * D * X;
+  x->SI = std::max((long long)D * D * D * X * X, std::max(x->S, (long long)D * D * X * X));
   x->trivial_bond.assign(x->Lmax + 1, 1);
   // original site offsets
   long long off = 0, hoff = 0;
@@ -1345,7 +1363,7 @@ int setup(pepsvmc_ctx* x, const double* tensors, const double* sketch) {
     }
   x->P = off;
   x->Ph = hoff;
-  x->sketch_host.assign(sketch, sketch + (size_t)x->Lmax * x->chi * D * x->chi);
+  x->sketch_host.assign(sketch, sketch + (size_t)x->Lmax * x->chi_x * D * x->chi_x);
 
   cudaError_t e;
 #define ALLOC(p, n) if ((e = x->alloc(&(p), (size_t)(n))) != cudaSuccess) return x->fail(PEPSVMC_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e))
@@ -1509,7 +1527,9 @@ int pepsvmc_init(const pepsvmc_config* cfg, const double* tensors, const double*
   x->Ly = cfg->Ly;
   x->Lx = cfg->Lx;
   x->D = cfg->D;
-  x->chi = cfg->chi;
+  x->chi = x->chi_s = cfg->chi;
+  x->chi_m = cfg->chi_measure ? cfg->chi_measure : cfg->chi;
+  x->chi_x = std::max(x->chi_s, x->chi_m);
   x->nfit = cfg->n_fit;
   return setup(x, tensors, sketch);
 }

@@ -308,3 +308,39 @@ def test_full_size_sampled_parity(api, name, decay, chains, tol):
         assert sg[c] == r["sign"]
         assert abs(lp[c] - r["logpsi"]) <= LOGPSI_TOL * max(1.0, abs(r["logpsi"]) / 100.0)
     ctx.close()
+
+
+def test_separate_sampling_and_measurement_cutoffs(api):
+    """A smaller cutoff for sampling than for measuring (Sec. II A, App. D): the sweep
+    truncates to Dc1 = 8 and matches the oracle's Dc = 8 sweep (decisions, final spins,
+    ratios); the measurement truncates to Dc2 = 16 and matches the oracle at Dc = 16
+    (E_loc, ln|Psi|, G) -- at these configurations E_loc moves by ~2 % between the two
+    cutoffs, so a measurement at the sampler's cutoff would fail by three decades."""
+    w = structured("peps_8x8", 4)
+    g = grid_of(w)
+    start = inputs.start_spins(4, 8, 8, 33, "random")
+    ctx = api.PepsVMC(8, 8, 4, 8, 4, w["tensors"], w["sketch"], J1=1.0, J2=0.0, seed=77, n_fit=3,
+                      chi_measure=16)
+    ctx.set_spins(start)
+    ctx.set_sweep_counter(3)
+    ctx.enable_trace(True)
+    ctx.sample_sweep(1)
+    ratio, dec = ctx.get_trace()
+    final = ctx.get_spins()
+    dev = []
+    for c in range(4):
+        tr = vmc.Trace(follow={b: int(dec[c, b]) for b in range(ctx.n_bonds) if dec[c, b] >= 0}, tie=1e-5)
+        new, _, _ = vmc.sweep(g, start[c], 8, w["sketch"], 3, 77, c, 3, trace=tr)
+        for bond, rho, u, acc in tr.rows:
+            assert int(acc) == int(dec[c, bond])
+            dev.append(abs(ratio[c, bond] - rho) / max(abs(rho), 1.0))
+        assert np.array_equal(new, final[c])
+    assert max(dev) <= RATIO_TOL_SWEEP and np.median(dev) <= MEDIAN_TOL_SWEEP
+    e, lp, sg = ctx.measure()
+    for c in range(4):
+        r = vmc.measure(g, final[c], 16, w["sketch"], 3, 1.0, 0.0)
+        assert abs(e[c] - r["eloc"]) <= ELOC_TOL * r["eloc_scale"], (c, e[c], r["eloc"])
+        assert sg[c] == r["sign"]
+        assert abs(lp[c] - r["logpsi"]) <= LOGPSI_TOL
+        check_grad(ctx.chain_grad(c), flat_G(r["G"]))
+    ctx.close()

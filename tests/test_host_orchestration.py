@@ -24,9 +24,12 @@ from paper_1908_09359_gb300 import inputs, api
 w = inputs.WORKLOADS[sys.argv[1]]
 L = max(w["Ly"], w["Lx"])
 t = inputs.peps_tensors(w["Ly"], w["Lx"], w["D"], 1)
+# the sampler at 2/3 of the cutoff, the measurement at the full cutoff (Dc1 < Dc2)
+chi_s = max(1, (2 * w["chi"]) // 3) if sys.argv[2] == "split" else w["chi"]
+chi_m = w["chi"] if sys.argv[2] == "split" else 0
 sk = np.zeros((L, w["chi"], w["D"], w["chi"]))
-c = api.PepsVMC(w["Ly"], w["Lx"], w["D"], w["chi"], w["n_chains"], t, sk, J1=w["J1"], J2=w["J2"],
-                seed=1, n_fit=3, stream=0)
+c = api.PepsVMC(w["Ly"], w["Lx"], w["D"], chi_s, w["n_chains"], t, sk, J1=w["J1"], J2=w["J2"],
+                seed=1, n_fit=3, stream=0, chi_measure=chi_m)
 n0 = c.launches
 c.sample_sweep(1)
 n1 = c.launches
@@ -47,11 +50,12 @@ print(json.dumps(dict(sweep=n1 - n0, measure=n2 - n1)))
 """
 
 
+@pytest.mark.parametrize("cutoffs", ["one", "split"])
 @pytest.mark.parametrize("name", list(inputs.WORKLOADS))
-def test_every_launch_in_bounds(name):
+def test_every_launch_in_bounds(name, cutoffs):
     build.build()
     env = dict(os.environ, PEPSVMC_DRY_RUN="1", PYTHONPATH=ROOT)
-    r = subprocess.run([sys.executable, "-c", SCRIPT, name], capture_output=True, text=True, env=env,
+    r = subprocess.run([sys.executable, "-c", SCRIPT, name, cutoffs], capture_output=True, text=True, env=env,
                        timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     counts = json.loads(r.stdout.strip().splitlines()[-1])
