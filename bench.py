@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--n-fit", type=int, default=3)
     p.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16", "tf32", "bf16x3"],
                    help="bf16x3 (split-BF16 tensor cores, the chosen form) or fp32 (plain)")
+    p.add_argument("--chi", type=int, default=None, help="sampling cutoff Dc1 (default: the workload's Dc)")
+    p.add_argument("--chi-measure", type=int, default=0,
+                   help="measurement cutoff Dc2 (default 0: the same as the sampling cutoff)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -217,8 +220,11 @@ def run_ours(args):
     seeds = rank_seeds(w, rank)
     spins = inputs.start_spins(C, w["Ly"], w["Lx"], seeds["spins"], "random")
     prec = api.PRECISIONS[args.precision]
-    ctx = api.PepsVMC(w["Ly"], w["Lx"], w["D"], w["chi"], C, w["tensors"], w["sketch"], J1=w["J1"],
-                      J2=w["J2"], seed=seeds["key"], n_fit=args.n_fit, precision=prec)
+    chi_s = args.chi or w["chi"]
+    chi_x = max(chi_s, args.chi_measure)
+    sk = w["sketch"] if chi_x == w["chi"] else inputs.sketch(max(w["Ly"], w["Lx"]), chi_x, w["D"], w["seed"])
+    ctx = api.PepsVMC(w["Ly"], w["Lx"], w["D"], chi_s, C, w["tensors"], sk, J1=w["J1"],
+                      J2=w["J2"], seed=seeds["key"], n_fit=args.n_fit, precision=prec, chi_measure=args.chi_measure)
     ctx.set_spins(spins)
     delta = 1e-3
 
@@ -353,7 +359,8 @@ def run_ours(args):
                                       "tf32": "tf32 operands, f32 accumulate",
                                       "bf16x3": "bf16 hi+lo operands, f32 accumulate"}[args.precision],
         "data": "synthetic (seeded iid N(0,1) PEPS tensors, random S^z=0 starts)",
-        "config": {"workload": args.workload, "Ly": w["Ly"], "Lx": w["Lx"], "D": w["D"], "Dc": w["chi"],
+        "config": {"workload": args.workload, "Ly": w["Ly"], "Lx": w["Lx"], "D": w["D"], "Dc": chi_s,
+                   "Dc_measure": args.chi_measure or chi_s,
                    "J1": w["J1"], "J2": w["J2"], "chains_per_gpu": C, "n_fit": args.n_fit,
                    "form": {"fp32": "plain FP32", "bf16": "mixed BF16 (tcgen05)", "tf32": "mixed TF32 (tcgen05)",
                             "bf16x3": "mixed split-BF16 (tcgen05)"}[args.precision], "step": "sweep + measure + gradient sums + sign-SGD",
