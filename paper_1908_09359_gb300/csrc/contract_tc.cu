@@ -203,24 +203,14 @@ __device__ __forceinline__ void load_tile(uint8_t* tile, const float* base, long
             f[j][q][i] = (row + q < nrows && k + i < K) ? src[q + (long long)i * s_k] : 0.f;
       }
     }
-    // A quad's four rows land in the same two 16-byte bank groups for every lane, so
-    // each lane starts at a different row of its quad ((r4 / 2) mod 4): per store the
-    // warp then covers all eight groups, four wavefronts instead of sixteen.
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       const int u = threadIdx.x + j * kThreads;
       if (u >= (ROWS / 4) * KC) break;
-      const int r4 = u % (ROWS / 4), r = r4 * 4, kc = u / (ROWS / 4);
-      const int rot = (r4 >> 1) & 3;
+      const int r = (u % (ROWS / 4)) * 4, kc = u / (ROWS / 4);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int qq = (q + rot) & 3;
-        float g[CE];
-#pragma unroll
-        for (int i = 0; i < CE; ++i)
-          g[i] = qq == 0 ? f[j][0][i] : qq == 1 ? f[j][1][i] : qq == 2 ? f[j][2][i] : f[j][3][i];
-        put16<EB, X3>(tile + (((r + qq) >> 3) * KC + kc) * 128 + ((r + qq) & 7) * 16, g, lo_off);
-      }
+      for (int q = 0; q < 4; ++q)
+        put16<EB, X3>(tile + (((r + q) >> 3) * KC + kc) * 128 + ((r + q) & 7) * 16, f[j][q], lo_off);
     }
   } else {
     for (int u = threadIdx.x; u < ROWS * KC; u += kThreads) {
