@@ -565,7 +565,8 @@ struct pepsvmc_ctx {
     return gemm(q);
   }
 
-  // Optimal site of the fit (App. B): Y (cV,Dd,cV2) = L (cT,Dl,cV) . T . a . R (cT2,Dr,cV2).
+  // Optimal site of the fit (App. B): Y (cV,Dd,cV2) = L (cT,Dl,cV) . T . a . R (cT2,Dr,cV2),
+  // contracted from the left; tmp2 keeps L . T . a for left3_tail_after_proj.
   cudaError_t proj3(const float* Lf, long long bsL, int cT, int cV, const float* T, long long bsT, int cT2,
                     const SiteOp& a, const float* Rf, long long bsR, int cV2, float* Y, long long bsY) {
     const int Dl = a.Dl, Dr = a.Dr, Du = a.Du, Dd = a.Dd;
