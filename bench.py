@@ -132,6 +132,27 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def binding_roofline(flops, nbytes, seconds, compute_peak, hbm_peak):
+    """(binding roof, other roof, flop per byte, ridge) of a kernel that did `flops`
+    algorithmic flops over `nbytes` algorithmic bytes in `seconds`.  compute_peak =
+    (bound name, TFLOP/s, source), hbm_peak = (GB/s, source).  The binding roof is HBM
+    when the intensity lies below the ridge point of the compute peak, else the compute
+    unit; each roof carries achieved, peak, unit and frac = achieved / peak."""
+    cbound, cpeak, csrc = compute_peak
+    hbm, hsrc = hbm_peak
+    intensity = flops / nbytes if nbytes > 0 else None
+    ridge = cpeak * 1e12 / (hbm * 1e9)
+    compute = {"bound": cbound, "achieved": flops / seconds / 1e12 if seconds > 0 else None, "peak": cpeak,
+               "unit": "TFLOP/s", "peak_source": csrc}
+    compute["frac"] = compute["achieved"] / cpeak if compute["achieved"] else None
+    memory = {"bound": "hbm", "achieved": nbytes / seconds / 1e9 if seconds > 0 else None, "peak": hbm,
+              "unit": "GB/s", "peak_source": hsrc}
+    memory["frac"] = memory["achieved"] / hbm if memory["achieved"] else None
+    if intensity is not None and intensity < ridge:
+        return memory, compute, intensity, ridge
+    return compute, memory, intensity, ridge
+
+
 def oracle_sample_seconds(name, reps=1):
     """Seconds per sample of the FP64 oracle on this host, from a bounded sample of the
     workload: one bulk-row truncation fit, one sampling row, one measurement row (three-
@@ -323,18 +344,9 @@ def run_ours(args):
                      args.precision] + ", tile autotuned per shape)")
         cbound = "tensor"
         csrc = src + {"bf16": "", "tf32": " x 1/2 for TF32", "bf16x3": " x 1/3 for three BF16 MMAs"}[args.precision]
-    flops, nbytes, gsec = prof["gemm_flops"], prof["gemm_bytes"], prof["gemm_ms"] / 1e3
-    intensity = flops / nbytes if nbytes > 0 else None
-    ridge = cpeak * 1e12 / (hbm * 1e9)
-    compute = {"bound": cbound, "achieved": flops / gsec / 1e12 if gsec > 0 else None, "peak": cpeak,
-               "unit": "TFLOP/s", "peak_source": csrc}
-    compute["frac"] = compute["achieved"] / cpeak if compute["achieved"] else None
-    memory = {"bound": "hbm", "achieved": nbytes / gsec / 1e9 if gsec > 0 else None, "peak": hbm,
-              "unit": "GB/s", "peak_source": hbm_src}
-    memory["frac"] = memory["achieved"] / hbm if memory["achieved"] else None
-    # The binding roofline: HBM when the contractions' algorithmic intensity lies below
-    # the ridge point of the compute peak, the compute unit otherwise.
-    bind, other = (memory, compute) if intensity is not None and intensity < ridge else (compute, memory)
+    bind, other, intensity, ridge = binding_roofline(prof["gemm_flops"], prof["gemm_bytes"], prof["gemm_ms"] / 1e3,
+                                                     (cbound, cpeak, csrc), (hbm, hbm_src))
+    flops, nbytes = prof["gemm_flops"], prof["gemm_bytes"]
     roofline = {
         "kernel": kname, "bound": bind["bound"], "achieved": bind["achieved"], "peak": bind["peak"],
         "unit": bind["unit"], "frac": bind["frac"], "peak_source": bind["peak_source"],
