@@ -464,3 +464,31 @@ def test_accumulator_gradient_formula():
     # site 1 slot 1 (sigma=-1) only in sample 1: <G E> = -1.5, <G> = 1.5, grad = -1.5 + 3 = 1.5
     assert grad[0][1][1].item() == pytest.approx(1.5)
     assert grad[0][1][0].item() == pytest.approx(-10.5 + 7.0)
+
+
+# ------------------------------------------------ P11: sequential vs random-NNASP sampling
+
+def test_random_nnasp_and_sequential_sweep_share_the_stationary_distribution():
+    """Sec. II A: the random-NNASP rule with its 1/K proposal factors and the sequential
+    sweep both leave |Psi|^2 invariant, so their stationary energies agree (the paper's
+    validation of the sequential scheme).  Exact transition matrices over the S^z = 0
+    sector of 2x4 (70 configurations); dropping the 1/K factors breaks detailed balance."""
+    from oracle import random_nnasp as rn
+    Ly, Lx = 2, 4
+    g = peps(Ly, Lx, 2, 77)
+    cfg, psi = rn.sector(g)
+    pi = psi ** 2 / np.sum(psi ** 2)
+    Pr = rn.random_scheme_matrix(cfg, psi, Ly, Lx)
+    Ps = rn.sequential_sweep_matrix(cfg, psi, Ly, Lx)
+    for P in (Pr, Ps):
+        assert np.allclose(P.sum(axis=1), 1.0, atol=1e-12) and np.all(P >= -1e-15)
+        assert np.max(np.abs(pi @ P - pi)) <= 1e-12
+    flow = pi[:, None] * Pr
+    assert np.max(np.abs(flow - flow.T)) <= 1e-12                      # detailed balance
+    assert np.max(np.abs(rn.stationary(Pr) - rn.stationary(Ps))) <= 1e-9
+    E, _, _ = exact.energy_exact(g, 1.0, 0.0)
+    eloc = np.array([vmc.measure(g, c, 4, sk(4, 4, 2), 1, 1.0, 0.0, want_grad=False)["eloc"] for c in cfg])
+    assert float(rn.stationary(Pr) @ eloc) == pytest.approx(E, abs=1e-10)
+    assert float(rn.stationary(Ps) @ eloc) == pytest.approx(E, abs=1e-10)
+    wrong = rn.random_scheme_matrix(cfg, psi, Ly, Lx, with_k=False)
+    assert np.max(np.abs(pi @ wrong - pi)) > 1e-4                      # the 1/K factors matter
