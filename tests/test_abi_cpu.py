@@ -46,7 +46,8 @@ def _cfg(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(Ly=3, Lx=3), dict(D=0), dict(chi=0), dict(n_fit=2),
-                                 dict(n_chains=0), dict(precision=7), dict(chi=64, D=16)])
+                                 dict(n_chains=0), dict(precision=7), dict(chi=64, D=16),
+                                 dict(chi_measure=-1), dict(chi_measure=65), dict(chi_measure=64, D=16)])
 def test_invalid_config_is_rejected_before_any_cuda_call(lib, bad):
     cfg = _cfg(**bad)
     t = np.zeros(10)
@@ -55,6 +56,17 @@ def test_invalid_config_is_rejected_before_any_cuda_call(lib, bad):
                           t.ctypes.data_as(C.POINTER(C.c_double)), None, C.byref(ctx))
     assert rc == _lib.EINVAL
     assert lib.pepsvmc_last_error(ctx).decode()
+    lib.pepsvmc_destroy(ctx)
+
+
+def test_reserved_fields_must_be_zero(lib):
+    cfg = _cfg()
+    cfg.reserved[2] = 1
+    t = np.zeros(10)
+    ctx = C.c_void_p()
+    rc = lib.pepsvmc_init(C.byref(cfg), t.ctypes.data_as(C.POINTER(C.c_double)),
+                          t.ctypes.data_as(C.POINTER(C.c_double)), None, C.byref(ctx))
+    assert rc == _lib.EINVAL and "reserved" in lib.pepsvmc_last_error(ctx).decode()
     lib.pepsvmc_destroy(ctx)
 
 
