@@ -61,7 +61,15 @@ typedef struct {
   int32_t chi_measure;  /* Dc of the measurement (E_loc, Psi, G), 0..64;    */
                         /* 0 = chi.  chi is then the sampler's Dc (Sec. II A */
                         /* and App. D use a smaller cutoff for sampling)    */
-  int32_t reserved[6];  /* must be zero                                    */
+  uint64_t wait_budget_cycles; /* clock budget of every device-side wait    */
+                        /* (tensor-core completion barriers); 0 = default   */
+                        /* (4e9 cycles, ~2 s).  A wait that runs out sets   */
+                        /* the status that the call returns as ETIMEOUT     */
+  int32_t chain_offset; /* global index of chain 0 in the Philox counters   */
+                        /* (>= 0): a job whose chains are split over several */
+                        /* contexts draws the same numbers as one context   */
+                        /* holding all of them                              */
+  int32_t reserved[3];  /* must be zero                                    */
 } pepsvmc_config;
 
 /* Create a context (on failure *out may still receive a context that holds the
@@ -89,6 +97,18 @@ int pepsvmc_set_spins(pepsvmc_ctx* ctx, const int8_t* spins);  /* host, n_chains
 int pepsvmc_get_spins(pepsvmc_ctx* ctx, int8_t* spins);
 int pepsvmc_set_tensors(pepsvmc_ctx* ctx, const double* tensors);
 int pepsvmc_get_tensors(pepsvmc_ctx* ctx, double* tensors);
+
+/* Fused three-line steps (on by default in the BF16 and split-BF16 precisions): the
+ * three products of a column step (App. C) run in one tensor-core kernel per chain and
+ * bond tile, with the intermediates kept in tensor and shared memory; bonds up to
+ * Dc = 32 and D = 8, larger ones use the separate products.  pepsvmc_set_fused(ctx, 0)
+ * computes every step as three separate products (same arithmetic type, other
+ * rounding order).  Forcing a contraction kernel (pepsvmc_set_contraction_kernel)
+ * also disables the fused steps.  Drops a captured step graph.                  */
+int pepsvmc_set_fused(pepsvmc_ctx* ctx, int32_t on);
+
+/* Change the device wait budget of an existing context (cycles; 0 = default).  */
+int pepsvmc_set_wait_budget(pepsvmc_ctx* ctx, uint64_t cycles);
 
 /* Sweep counter used in the Metropolis Philox counter (chain, sweep, bond, tag). */
 int pepsvmc_set_sweep_counter(pepsvmc_ctx* ctx, uint64_t sweep);
@@ -143,6 +163,24 @@ int pepsvmc_amplitude(pepsvmc_ctx* ctx, int32_t row, double* logpsi, int8_t* sig
 int pepsvmc_energy_and_grad(pepsvmc_ctx* ctx, int32_t n_sweeps, double* E_mean, double* E_var,
                             double* eloc, double* logpsi, int8_t* sign, double* grad);
 
+/* The float64 sums behind the gradient of the last pepsvmc_energy_and_grad
+ * (Algorithm 1: E_tot, E_tot^2 and the sample count, then P1 = sum G E_loc and
+ * P2 = sum G per packed tensor entry), for a job whose chains are split over
+ * several contexts (one per GPU): each rank reads its sums, the ranks add them
+ * (an all-reduce), and every rank writes the totals back with pepsvmc_set_sums,
+ * which recomputes dE/dA = P1/n - (P2/n) E_tot/n exactly as energy_and_grad does,
+ * so that the following pepsvmc_update applies one identical sign-SGD step on
+ * every rank.  Host buffers: scalars[3] = {sum E, sum E^2, n}, sumGE and sumG with
+ * pepsvmc_n_params entries each (nullable in get).
+ * pepsvmc_sums_device exposes the same three device arrays (owned by the context,
+ * valid until pepsvmc_destroy) so that a collective library can reduce them in
+ * place; pepsvmc_finalize_sums then recomputes the gradient from them.
+ * Errors: ESTATE before any energy_and_grad; EINVAL (null pointers, n <= 0).    */
+int pepsvmc_get_sums(pepsvmc_ctx* ctx, double* scalars, double* sumGE, double* sumG);
+int pepsvmc_set_sums(pepsvmc_ctx* ctx, const double* scalars, const double* sumGE, const double* sumG);
+int pepsvmc_sums_device(pepsvmc_ctx* ctx, double** scalars, double** sumGE, double** sumG);
+int pepsvmc_finalize_sums(pepsvmc_ctx* ctx);
+
 /* Sign-SGD (Sec. II B, Eq. (10)) with the gradient of the last
  * pepsvmc_energy_and_grad: A <- A - r * delta * sgn(dE/dA), r = Philox uniform
  * with counter (element & 0xffffffff, element >> 32, step, tag).
@@ -166,6 +204,25 @@ int pepsvmc_env3_left(pepsvmc_ctx* ctx, const float* E, const float* T, const fl
                       const int8_t* spins, const float* B, float* out, int32_t n_chains,
                       int32_t cT, int32_t cB, int32_t cT2, int32_t cB2,
                       int32_t Dl, int32_t Dr, int32_t Du, int32_t Dd);
+
+/* Four-line environment step of a row pair (App. C: the environments that close the
+ * vertical and diagonal amplitude ratios of E_loc) for n_chains chains, on the context's
+ * stream with the context's scratch:
+ *   out[c](a',r1,r2,b') = sum over a,l1,l2,b,u1,d1,d2 of
+ *       E[c](a,l1,l2,b) * T[c](a,u1,a') * A1_{s1}(l1,r1,u1,d1) * A2_{s2}(l2,r2,d1,d2) * B[c](b,d2,b')
+ * E: (cT, D1l, D2l, cB); T: top boundary-MPS site (cT, Du1, cT2); B: bottom site
+ * (cB, Dd2, cB2); out: (cT2, D1r, D2r, cB2); float32 device arrays, row-major per chain,
+ * chains back to back.  A1, A2: the upper and lower site tensors, both spin slots, each
+ * slot in the order (l, u, r, d) (A2's up leg is A1's down leg, Dd1); chain c uses slot 1
+ * of A1 when spins1[c] < 0 and of A2 when spins2[c] < 0 (int8 device arrays), slot 0
+ * otherwise or when the pointer is NULL.  In the tensor-core precisions bonds up to
+ * Dc = 32 and D = 8 run as one fused kernel.  Asynchronous on the stream.
+ * Errors: EINVAL (null pointers, non-positive sizes, more chains than the context's or
+ * intermediates larger than its scratch); ECUDA.                                     */
+int pepsvmc_env4_left(pepsvmc_ctx* ctx, const float* E, const float* T, const float* A1, const int8_t* spins1,
+                      const float* A2, const int8_t* spins2, const float* B, float* out, int32_t n_chains,
+                      int32_t cT, int32_t cB, int32_t cT2, int32_t cB2, int32_t D1l, int32_t D1r, int32_t Du1,
+                      int32_t Dd1, int32_t D2l, int32_t D2r, int32_t Dd2);
 
 /* pepsvmc_env3_left without a context and without allocating anything (the paper
  * has no counterpart; this is a library convenience).  For callers that cannot

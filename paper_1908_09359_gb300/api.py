@@ -32,12 +32,14 @@ class PepsVMC:
     """
 
     def __init__(self, Ly, Lx, D, chi, n_chains, tensors, sketch, J1=1.0, J2=0.0, seed=0, n_fit=3,
-                 precision=FP32, stream=None, chi_measure=0):
+                 precision=FP32, stream=None, chi_measure=0, wait_budget_cycles=0, chain_offset=0):
         self.lib = _lib.load()
         cfg = _lib.Config()
         cfg.Ly, cfg.Lx, cfg.D, cfg.chi, cfg.n_chains, cfg.n_fit = Ly, Lx, D, chi, n_chains, n_fit
         cfg.J1, cfg.J2, cfg.seed, cfg.precision = float(J1), float(J2), int(seed), int(precision)
         cfg.chi_measure = int(chi_measure)
+        cfg.wait_budget_cycles = int(wait_budget_cycles)
+        cfg.chain_offset = int(chain_offset)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -178,6 +180,13 @@ class PepsVMC:
         self._check(self.lib.pepsvmc_env3_left(self.ctx, ptr(E), ptr(T), ptr(A), ptr(spins), ptr(B), ptr(out),
                                                *[int(v) for v in dims]))
 
+    def env4_left(self, E, T, A1, spins1, A2, spins2, B, out, dims):
+        """Four-line environment step on device tensors; ``dims`` = (n_chains, cT, cB, cT2,
+        cB2, D1l, D1r, Du1, Dd1, D2l, D2r, Dd2)."""
+        ptr = lambda t: C.c_void_p(t if isinstance(t, int) else (t.data_ptr() if t is not None else 0))  # noqa: E731
+        self._check(self.lib.pepsvmc_env4_left(self.ctx, ptr(E), ptr(T), ptr(A1), ptr(spins1), ptr(A2), ptr(spins2),
+                                               ptr(B), ptr(out), *[int(v) for v in dims]))
+
     def get_profile_shapes(self):
         import json
         buf = C.create_string_buffer(1 << 20)
@@ -261,6 +270,40 @@ class PepsVMC:
 
     def update(self, delta, step):
         self._check(self.lib.pepsvmc_update(self.ctx, float(delta), int(step)))
+
+    def set_fused(self, on=True):
+        self._check(self.lib.pepsvmc_set_fused(self.ctx, 1 if on else 0))
+
+    def set_wait_budget(self, cycles):
+        self._check(self.lib.pepsvmc_set_wait_budget(self.ctx, int(cycles)))
+
+    # ------------------------------------------------- gradient sums (multi-rank jobs)
+    def get_sums(self):
+        """(scalars[3] = sum E, sum E^2, n; sumGE; sumG) of the last energy_and_grad."""
+        sc = np.empty(3)
+        ge = np.empty(self.n_params)
+        g = np.empty(self.n_params)
+        self._check(self.lib.pepsvmc_get_sums(self.ctx, _dp(sc), _dp(ge), _dp(g)))
+        return sc, ge, g
+
+    def set_sums(self, scalars, sumGE, sumG):
+        """Replace the sums (e.g. by their all-reduced totals) and recompute the gradient."""
+        sc = np.ascontiguousarray(scalars, dtype=np.float64)
+        ge = np.ascontiguousarray(sumGE, dtype=np.float64)
+        g = np.ascontiguousarray(sumG, dtype=np.float64)
+        if sc.size != 3 or ge.size != self.n_params or g.size != self.n_params:
+            raise ValueError("set_sums: scalars must have 3 entries, sumGE and sumG n_params each")
+        self._check(self.lib.pepsvmc_set_sums(self.ctx, _dp(sc), _dp(ge), _dp(g)))
+
+    def sums_device(self):
+        """Device addresses (scalars, sumGE, sumG) of the context's float64 sums."""
+        a, b, c = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        self._check(self.lib.pepsvmc_sums_device(self.ctx, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def finalize_sums(self):
+        """Recompute the gradient from the device sums (after an in-place reduction)."""
+        self._check(self.lib.pepsvmc_finalize_sums(self.ctx))
 
 
 def env3_left_noalloc(E, T, A, spins, B, out, dims, stream=None):

@@ -32,7 +32,11 @@ struct GemmDesc {
   float alpha = 1.f;
   const double* inv_scale = nullptr;
   int accumulate = 0;
+  long long wait_cycles = 0;  // clock budget of each device-side wait (0 = kDefaultWaitCycles)
 };
+
+// Default clock budget of a device-side wait (~2 s at 2 GHz).
+constexpr long long kDefaultWaitCycles = 4000000000LL;
 
 // Tile configurations of the FP32 contraction kernel (index into a fixed table).
 int gemm_f32_num_configs();

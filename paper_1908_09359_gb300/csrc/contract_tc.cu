@@ -15,131 +15,16 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tc_util.cuh"
 
 namespace pv {
 namespace {
 
+using namespace tc;
+
 constexpr int kBM = 128;       // rows per tile = MMA M
 constexpr int kKBytes = 128;   // bytes of K per stage (64 BF16 or 32 TF32)
 constexpr int kThreads = 256;  // 8 warps; warps w and w+4 share TMEM lane quarter w%4 in the epilogue
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor: start >> 4 (bits 0-13), leading (K) core-matrix
-// offset >> 4 (bits 16-29), stride (8-row group) offset >> 4 (bits 32-45), version 1
-// (bits 46-47), no swizzle (bits 61-63 = 0).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
-
-// Instruction descriptor of kind::f16 / kind::tf32: D = F32 (bits 4-5 = 1), A and B
-// format (bits 7-9, 10-12: BF16 = 1, TF32 = 2), both K-major, N >> 3 (bits 17-22),
-// M >> 4 (bits 24-28).
-template <int EB>
-__device__ __forceinline__ uint32_t idesc(int M, int N) {
-  const uint32_t f = (EB == 2) ? 1u : 2u;
-  return (1u << 4) | (f << 7) | (f << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-template <int EB>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  if constexpr (EB == 2) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
-  } else {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
-  }
-}
-
-__device__ __forceinline__ void commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  const long long t0 = clock64();
-  while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
-  }
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld1_nowait(uint32_t taddr, float& v) {
-  uint32_t r;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-  v = __uint_as_float(r);
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// TF32 operand: round to nearest (the tensor core itself would drop the low bits).
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t u;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
-  return __uint_as_float(u);
-}
-
-// Write CE values (one 16-byte core-matrix row) converted to the operand type.  With
-// X3 the BF16 value goes to dst and the BF16 rounding of its remainder to dst + lo_off.
-template <int EB, bool X3 = false>
-__device__ __forceinline__ void put16(uint8_t* dst, const float* f, int lo_off = 0) {
-  if constexpr (X3) {
-    uint32_t w[4], wl[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
-      const float2 hf = __bfloat1622float2(h);
-      const __nv_bfloat162 l = __floats2bfloat162_rn(f[2 * i] - hf.x, f[2 * i + 1] - hf.y);
-      w[i] = *reinterpret_cast<const uint32_t*>(&h);
-      wl[i] = *reinterpret_cast<const uint32_t*>(&l);
-    }
-    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-    *reinterpret_cast<uint4*>(dst + lo_off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-  } else if constexpr (EB == 2) {
-    uint32_t w[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
-      w[i] = *reinterpret_cast<const uint32_t*>(&h);
-    }
-    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-  } else {
-    *reinterpret_cast<float4*>(dst) = make_float4(to_tf32(f[0]), to_tf32(f[1]), to_tf32(f[2]), to_tf32(f[3]));
-  }
-}
-
-__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Fill one operand tile (rows x kKBytes) of stage memory, K-major core-matrix layout:
 // core matrix (r/8, kc) at ((r/8) * KC + kc) * 128 bytes, row r%8 at +16 (r%8).
@@ -279,12 +164,15 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(const GemmDesc d, uns
   const uint32_t id = idesc<EB>(kBM, BN);
 
   const int nk = (d.K + BK - 1) / BK;
+  const long long budget = d.wait_cycles > 0 ? d.wait_cycles : kDefaultWaitCycles;
+  // draining after a timeout waits at least the default budget for the MMAs in flight
+  const long long drain = budget > kDefaultWaitCycles ? budget : kDefaultWaitCycles;
   uint32_t phase[2] = {0u, 0u};
   bool ok = true;
   for (int kt = 0; kt < nk && ok; ++kt) {
     const int s = kt % STAGES;
     if (kt >= STAGES) {
-      const bool w = wait_parity(&bar[s], phase[s]);
+      const bool w = wait_parity(&bar[s], phase[s], budget);
       phase[s] ^= 1u;
       ok = !__syncthreads_or(!w);
       if (!ok) break;
@@ -316,12 +204,12 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(const GemmDesc d, uns
   }
   if (ok && nk > 0) {
     const int s = (nk - 1) % STAGES;
-    ok = !__syncthreads_or(!wait_parity(&bar[s], phase[s]));
+    ok = !__syncthreads_or(!wait_parity(&bar[s], phase[s], budget));
   }
   if (!ok) {
     if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
     // drain whatever is still in flight before giving the tensor memory back
-    if (nk > 0) wait_parity(&bar[(nk - 1) % STAGES], phase[(nk - 1) % STAGES]);
+    if (nk > 0) wait_parity(&bar[(nk - 1) % STAGES], phase[(nk - 1) % STAGES], drain);
   } else if (nk > 0) {
     tc_after_sync();
     float alpha = d.alpha;

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fused.cuh"
 #include "kernels.cuh"
 #include "pepsvmc.h"
 #include "proposal.cuh"
@@ -99,6 +100,8 @@ struct pepsvmc_ctx {
   std::vector<int> site_size;
   std::vector<long long> perm_site_off[4];
   long long launches = 0;
+  long long wait_budget = 0;  // device wait budget in clock cycles (0 = default)
+  unsigned chain_base = 0;    // global index of chain 0 in the Philox counters
   unsigned long long sweep_counter = 0;
   bool top_valid = false, have_grad = false, have_measure = false;
   int trace_on = 0;
@@ -343,7 +346,9 @@ struct pepsvmc_ctx {
              g.sCn2, g.sCn3);
     return k;
   }
-  cudaError_t run_choice(const GemmDesc& g, int choice) {
+  cudaError_t run_choice(const GemmDesc& g0, int choice) {
+    GemmDesc g = g0;
+    g.wait_cycles = wait_budget;
     if (choice >= 1000) return gemm_tc(g, 6, choice - 1000, status, st);  // split BF16, two stages
     if (choice >= 100) return gemm_tc(g, tc_mode(), choice - 100, status, st);
     return gemm_f32(g, choice, st);
@@ -394,7 +399,7 @@ struct pepsvmc_ctx {
       if (it != tuned.end()) return run_choice(g, it->second);
     }
     if (tc_mode() && (long long)g.M * g.N * g.K >= kTcMinWork && g.M >= 64 && g.K >= 8)
-      return gemm_tc(g, tc_mode(), 0, status, st);
+      return run_choice(g, 100);
     return gemm_f32(g, gemm_f32_pick(g), st);
   }
   static constexpr long long kTcMinWork = 1 << 15;
@@ -460,10 +465,161 @@ struct pepsvmc_ctx {
   }
 
   // --------------------------------------------------------- contractions
+  // Fused three-line step (all three products in one tensor-core kernel, intermediates
+  // on chip) for the tensor-core precisions; on by default, switchable for comparisons.
+  bool fused_on = true;
+  bool fused_ok(int cT, int cB, int cT2, int cB2, const SiteOp& a) const {
+    return fused_on && forced < 0 && (tc_mode() == 2 || tc_mode() == 3) &&
+           env3_fused_fits(cT, cB, cT2, cB2, a.Dl, a.Dr, a.Du, a.Dd);
+  }
+  // caller_memory: the operands are the caller's (the C-ABI step), not the context's
+  // allocations, so the context's bounds table does not cover them
+  cudaError_t fused3(Env3Fused f, int batch = 0, bool caller_memory = false) {
+    f.batch = batch > 0 ? batch : C;
+    f.wait_cycles = wait_budget;
+    const long long b1 = f.batch - 1;
+    if (!caller_memory && (!span(f.E, b1 * f.bsE + (f.cT - 1) * f.sEa + (f.Dl - 1) * f.sEl + (f.cB - 1) * f.sEb, 4, "fused E") ||
+        !span(f.T, b1 * f.bsT + (f.cT - 1) * f.sTa + (f.Du - 1) * f.sTu + (f.cT2 - 1) * f.sTa2, 4, "fused T") ||
+        !span(f.A, f.ssA + (f.Dl - 1) * f.sAl + (f.Du - 1) * f.sAu + (f.Dr - 1) * f.sAr + (f.Dd - 1) * f.sAd, 4,
+              "fused A") ||
+        !span(f.B, b1 * f.bsB + (f.cB - 1) * f.sBb + (f.Dd - 1) * f.sBd + (f.cB2 - 1) * f.sBb2, 4, "fused B") ||
+        !span(f.out, b1 * f.bsO + (f.cT2 - 1) * f.sOa2 + (f.Dr - 1) * f.sOr + (f.cB2 - 1) * f.sOb2, 4, "fused out") ||
+        (f.sel && !span(f.sel, b1 * f.sel_stride, 1, "fused spin selector"))))
+      return cudaErrorInvalidValue;
+    ++launches;
+    const double nb = f.batch;
+    const double flops = 2.0 * nb *
+        ((double)f.Dl * f.cB * f.Du * f.cT2 * f.cT + (double)f.cB * f.cT2 * f.Dr * f.Dd * f.Dl * f.Du +
+         (double)f.cT2 * f.Dr * f.cB2 * f.cB * f.Dd);
+    if (prof) {
+      prof_acc[0] += 1;
+      prof_acc[1] += flops;
+      // algorithmic bytes of the fused step: E, T, B and the result per chain, both slots of A once
+      prof_acc[5] += 4.0 * ((f.bsE ? nb : 1.0) * f.cT * f.Dl * f.cB + (f.bsT ? nb : 1.0) * f.cT * f.Du * f.cT2 +
+                            (f.bsB ? nb : 1.0) * f.cB * f.Dd * f.cB2 + nb * f.cT2 * f.Dr * f.cB2 +
+                            2.0 * f.Dl * f.Du * f.Dr * f.Dd);
+    }
+    char key[96];
+    snprintf(key, sizeof(key), "fused3 %d %d %d %d x %d %d %d %d", f.cT, f.cB, f.cT2, f.cB2, f.Dl, f.Dr, f.Du, f.Dd);
+    const bool split = tc_mode() == 3;
+    return timed(0, [&] { return env3_fused(f, split, status, st); }, key, flops);
+  }
+  // left step: E (cT,Dl,cB), T (cT,Du,cT2), B (cB,Dd,cB2) -> out (cT2,Dr,cB2)
+  Env3Fused fused_left(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
+                       const SiteOp& a, int flip, const float* B, long long bsB, int cB2, float* out,
+                       long long bsO) const {
+    Env3Fused f;
+    f.cT = cT; f.cB = cB; f.cT2 = cT2; f.cB2 = cB2; f.Dl = a.Dl; f.Dr = a.Dr; f.Du = a.Du; f.Dd = a.Dd;
+    f.E = E; f.bsE = bsE; f.sEa = (long long)a.Dl * cB; f.sEl = cB; f.sEb = 1;
+    f.T = T; f.bsT = bsT; f.sTa = (long long)a.Du * cT2; f.sTu = cT2; f.sTa2 = 1;
+    f.A = a.lurd; f.ssA = a.size;
+    f.sAl = (long long)a.Du * a.Dr * a.Dd; f.sAu = (long long)a.Dr * a.Dd; f.sAr = a.Dd; f.sAd = 1;
+    f.sel = (sel_base ? sel_base : spins) + a.spin; f.sel_stride = (long long)Ly * Lx; f.sel_xor = flip;
+    f.B = B; f.bsB = bsB; f.sBb = (long long)a.Dd * cB2; f.sBd = cB2; f.sBb2 = 1;
+    f.out = out; f.bsO = bsO; f.sOa2 = (long long)a.Dr * cB2; f.sOr = cB2; f.sOb2 = 1;
+    return f;
+  }
+  // right step as a mirrored left step: E (cT2,Dr,cB2), T (cT,Du,cT2), B (cB,Dd,cB2) -> out (cT,Dl,cB)
+  Env3Fused fused_right(const float* E, long long bsE, int cT2, int cB2, const float* T, long long bsT, int cT,
+                        const SiteOp& a, int flip, const float* B, long long bsB, int cB, float* out,
+                        long long bsO) const {
+    Env3Fused f;
+    f.cT = cT2; f.cB = cB2; f.cT2 = cT; f.cB2 = cB; f.Dl = a.Dr; f.Dr = a.Dl; f.Du = a.Du; f.Dd = a.Dd;
+    f.E = E; f.bsE = bsE; f.sEa = (long long)a.Dr * cB2; f.sEl = cB2; f.sEb = 1;
+    f.T = T; f.bsT = bsT; f.sTa = 1; f.sTu = cT2; f.sTa2 = (long long)a.Du * cT2;
+    f.A = a.lurd; f.ssA = a.size;
+    f.sAl = a.Dd; f.sAu = (long long)a.Dr * a.Dd; f.sAr = (long long)a.Du * a.Dr * a.Dd; f.sAd = 1;
+    f.sel = (sel_base ? sel_base : spins) + a.spin; f.sel_stride = (long long)Ly * Lx; f.sel_xor = flip;
+    f.B = B; f.bsB = bsB; f.sBb = 1; f.sBd = cB2; f.sBb2 = (long long)a.Dd * cB2;
+    f.out = out; f.bsO = bsO; f.sOa2 = (long long)a.Dl * cB; f.sOr = cB; f.sOb2 = 1;
+    return f;
+  }
+
+  // Fused four-line step (four products in one tensor-core kernel).
+  cudaError_t fused4(Env4Fused f) {
+    f.batch = C;
+    f.wait_cycles = wait_budget;
+    const long long b1 = C - 1;
+    if (!span(f.E, b1 * f.bsE + (f.cT - 1) * f.sEa + (f.D1l - 1) * f.sEl1 + (f.D2l - 1) * f.sEl2 + (f.cB - 1) * f.sEb,
+              4, "fused4 E") ||
+        !span(f.T, b1 * f.bsT + (f.cT - 1) * f.sTa + (f.Du1 - 1) * f.sTu + (f.cT2 - 1) * f.sTa2, 4, "fused4 T") ||
+        !span(f.A1, f.ss1 + (f.D1l - 1) * f.s1l + (f.Du1 - 1) * f.s1u + (f.D1r - 1) * f.s1r + (f.Dd1 - 1) * f.s1d, 4,
+              "fused4 a1") ||
+        !span(f.A2, f.ss2 + (f.D2l - 1) * f.s2l + (f.Dd1 - 1) * f.s2u + (f.D2r - 1) * f.s2r + (f.Dd2 - 1) * f.s2d, 4,
+              "fused4 a2") ||
+        !span(f.B, b1 * f.bsB + (f.cB - 1) * f.sBb + (f.Dd2 - 1) * f.sBd + (f.cB2 - 1) * f.sBb2, 4, "fused4 B") ||
+        !span(f.out, b1 * f.bsO + (f.cT2 - 1) * f.sOa2 + (f.D1r - 1) * f.sOr1 + (f.D2r - 1) * f.sOr2 +
+                         (f.cB2 - 1) * f.sOb2, 4, "fused4 out") ||
+        !span(f.sel1, b1 * f.sel_stride, 1, "fused4 spin 1") || !span(f.sel2, b1 * f.sel_stride, 1, "fused4 spin 2"))
+      return cudaErrorInvalidValue;
+    ++launches;
+    const double nb = C;
+    const double flops = 2.0 * nb *
+        ((double)f.D1l * f.D2l * f.cB * f.Du1 * f.cT2 * f.cT + (double)f.D2l * f.cB * f.cT2 * f.D1r * f.Dd1 * f.D1l * f.Du1 +
+         (double)f.cB * f.cT2 * f.D1r * f.D2r * f.Dd2 * f.D2l * f.Dd1 + (double)f.cT2 * f.D1r * f.D2r * f.cB2 * f.cB * f.Dd2);
+    if (prof) {
+      prof_acc[0] += 1;
+      prof_acc[1] += flops;
+      prof_acc[5] += 4.0 * ((f.bsE ? nb : 1.0) * f.cT * f.D1l * f.D2l * f.cB + (f.bsT ? nb : 1.0) * f.cT * f.Du1 * f.cT2 +
+                            (f.bsB ? nb : 1.0) * f.cB * f.Dd2 * f.cB2 + nb * f.cT2 * f.D1r * f.D2r * f.cB2 +
+                            2.0 * f.D1l * f.Du1 * f.D1r * f.Dd1 + 2.0 * f.D2l * f.Dd1 * f.D2r * f.Dd2);
+    }
+    char key[96];
+    snprintf(key, sizeof(key), "fused4 %d %d %d %d", f.cT, f.cB, f.cT2, f.cB2);
+    const bool split = tc_mode() == 3;
+    return timed(0, [&] { return env4_fused(f, split, status, st); }, key, flops);
+  }
+  bool fused4_ok(const Env4Fused& f) const {
+    return fused_on && forced < 0 && (tc_mode() == 2 || tc_mode() == 3) && env4_fused_fits(f);
+  }
+  // left step of rows (k,k+1): E (cT,D1l,D2l,cB), T (cT,Du1,cT2), B (cB,Dd2,cB2) -> out (cT2,D1r,D2r,cB2)
+  Env4Fused fused4_left(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
+                        const SiteOp& a1, int f1, const SiteOp& a2, int f2, const float* B, long long bsB, int cB2,
+                        float* out, long long bsO) const {
+    Env4Fused f;
+    f.cT = cT; f.cB = cB; f.cT2 = cT2; f.cB2 = cB2;
+    f.D1l = a1.Dl; f.D1r = a1.Dr; f.Du1 = a1.Du; f.Dd1 = a1.Dd; f.D2l = a2.Dl; f.D2r = a2.Dr; f.Dd2 = a2.Dd;
+    f.E = E; f.bsE = bsE; f.sEa = (long long)a1.Dl * a2.Dl * cB; f.sEl1 = (long long)a2.Dl * cB; f.sEl2 = cB; f.sEb = 1;
+    f.T = T; f.bsT = bsT; f.sTa = (long long)a1.Du * cT2; f.sTu = cT2; f.sTa2 = 1;
+    f.A1 = a1.lurd; f.ss1 = a1.size;
+    f.s1l = (long long)a1.Du * a1.Dr * a1.Dd; f.s1u = (long long)a1.Dr * a1.Dd; f.s1r = a1.Dd; f.s1d = 1;
+    f.A2 = a2.lurd; f.ss2 = a2.size;
+    f.s2l = (long long)a2.Du * a2.Dr * a2.Dd; f.s2u = (long long)a2.Dr * a2.Dd; f.s2r = a2.Dd; f.s2d = 1;
+    const int8_t* sb = sel_base ? sel_base : spins;
+    f.sel1 = sb + a1.spin; f.sel2 = sb + a2.spin; f.sel_stride = (long long)Ly * Lx; f.xor1 = f1; f.xor2 = f2;
+    f.B = B; f.bsB = bsB; f.sBb = (long long)a2.Dd * cB2; f.sBd = cB2; f.sBb2 = 1;
+    f.out = out; f.bsO = bsO; f.sOa2 = (long long)a1.Dr * a2.Dr * cB2; f.sOr1 = (long long)a2.Dr * cB2; f.sOr2 = cB2;
+    f.sOb2 = 1;
+    return f;
+  }
+  // right step as a mirrored left step: E (cT2,D1r,D2r,cB2) -> out (cT,D1l,D2l,cB)
+  Env4Fused fused4_right(const float* E, long long bsE, int cT2, int cB2, const float* T, long long bsT, int cT,
+                         const SiteOp& a1, int f1, const SiteOp& a2, int f2, const float* B, long long bsB, int cB,
+                         float* out, long long bsO) const {
+    Env4Fused f;
+    f.cT = cT2; f.cB = cB2; f.cT2 = cT; f.cB2 = cB;
+    f.D1l = a1.Dr; f.D1r = a1.Dl; f.Du1 = a1.Du; f.Dd1 = a1.Dd; f.D2l = a2.Dr; f.D2r = a2.Dl; f.Dd2 = a2.Dd;
+    f.E = E; f.bsE = bsE; f.sEa = (long long)a1.Dr * a2.Dr * cB2; f.sEl1 = (long long)a2.Dr * cB2; f.sEl2 = cB2;
+    f.sEb = 1;
+    f.T = T; f.bsT = bsT; f.sTa = 1; f.sTu = cT2; f.sTa2 = (long long)a1.Du * cT2;
+    f.A1 = a1.lurd; f.ss1 = a1.size;
+    f.s1l = a1.Dd; f.s1u = (long long)a1.Dr * a1.Dd; f.s1r = (long long)a1.Du * a1.Dr * a1.Dd; f.s1d = 1;
+    f.A2 = a2.lurd; f.ss2 = a2.size;
+    f.s2l = a2.Dd; f.s2u = (long long)a2.Dr * a2.Dd; f.s2r = (long long)a2.Du * a2.Dr * a2.Dd; f.s2d = 1;
+    const int8_t* sb = sel_base ? sel_base : spins;
+    f.sel1 = sb + a1.spin; f.sel2 = sb + a2.spin; f.sel_stride = (long long)Ly * Lx; f.xor1 = f1; f.xor2 = f2;
+    f.B = B; f.bsB = bsB; f.sBb = 1; f.sBd = cB2; f.sBb2 = (long long)a2.Dd * cB2;
+    f.out = out; f.bsO = bsO; f.sOa2 = (long long)a1.Dl * a2.Dl * cB; f.sOr1 = (long long)a2.Dl * cB; f.sOr2 = cB;
+    f.sOb2 = 1;
+    return f;
+  }
+
   // Three-line left step (App. C, Fig. "contraction" (c)): E (cT,Dl,cB) -> out (cT2,Dr,cB2).
   cudaError_t left3(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
                     const SiteOp& a, int flip, const float* B, long long bsB, int cB2, float* out,
                     long long bsO) {
+    if (fused_ok(cT, cB, cT2, cB2, a))
+      return fused3(fused_left(E, bsE, cT, cB, T, bsT, cT2, a, flip, B, bsB, cB2, out, bsO));
     GemmDesc g[3];
     env3_left_descs(g, Env3Dims{cT, cB, cT2, cB2, a.Dl, a.Dr, a.Du, a.Dd}, E, bsE, T, bsT, a.lurd, a.size,
                     spins + a.spin, (long long)Ly * Lx, flip, B, bsB, out, bsO, tmp1, tmp2, SI);
@@ -472,12 +628,21 @@ struct pepsvmc_ctx {
   }
   // Left step for the configuration and, when out1 is given, with the spin of the site
   // flipped: the first product E . T does not depend on the spin and is done once;
-  // tmp1 keeps it afterwards (delta3_after_left3 reads it).
+  // tmp1 keeps it afterwards (delta3_after_left3 reads it; keep_et asks for it when the
+  // fused kernel, which keeps E . T on chip, computes the step).
   cudaError_t left3_pair(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
                          const SiteOp& a, const float* B, long long bsB, int cB2, float* out0, float* out1,
-                         long long bsO) {
+                         long long bsO, bool keep_et = false) {
     GemmDesc g[3];
     const Env3Dims d{cT, cB, cT2, cB2, a.Dl, a.Dr, a.Du, a.Dd};
+    if (fused_ok(cT, cB, cT2, cB2, a)) {
+      PV_CUDA(fused3(fused_left(E, bsE, cT, cB, T, bsT, cT2, a, 0, B, bsB, cB2, out0, bsO)));
+      if (out1) PV_CUDA(fused3(fused_left(E, bsE, cT, cB, T, bsT, cT2, a, 1, B, bsB, cB2, out1, bsO)));
+      if (!keep_et) return cudaSuccess;
+      env3_left_descs(g, d, E, bsE, T, bsT, a.lurd, a.size, spins + a.spin, (long long)Ly * Lx, 0, B, bsB, out0,
+                      bsO, tmp1, tmp2, SI);
+      return gemm(g[0]);
+    }
     env3_left_descs(g, d, E, bsE, T, bsT, a.lurd, a.size, spins + a.spin, (long long)Ly * Lx, 0, B, bsB, out0, bsO,
                     tmp1, tmp2, SI);
     for (int i = 0; i < 3; ++i) PV_CUDA(gemm(g[i]));
@@ -492,6 +657,8 @@ struct pepsvmc_ctx {
   cudaError_t right3(const float* E, long long bsE, int cT2, int cB2, const float* T, long long bsT, int cT,
                      const SiteOp& a, int flip, const float* B, long long bsB, int cB, float* out,
                      long long bsO) {
+    if (fused_ok(cT2, cB2, cT, cB, a))
+      return fused3(fused_right(E, bsE, cT2, cB2, T, bsT, cT, a, flip, B, bsB, cB, out, bsO));
     PV_CUDA(right3_head(E, bsE, cT2, cB2, T, bsT, cT, a, flip));
     return right3_tail(a, cT, cB2, B, bsB, cB, out, bsO);
   }
@@ -520,6 +687,10 @@ struct pepsvmc_ctx {
   cudaError_t right3_pair(const float* E, long long bsE, int cT2, int cB2, const float* T, long long bsT, int cT,
                           const SiteOp& a, const float* B, long long bsB, int cB, float* out0, float* out1,
                           long long bsO) {
+    if (fused_ok(cT2, cB2, cT, cB, a)) {
+      PV_CUDA(fused3(fused_right(E, bsE, cT2, cB2, T, bsT, cT, a, 0, B, bsB, cB, out0, bsO)));
+      return fused3(fused_right(E, bsE, cT2, cB2, T, bsT, cT, a, 1, B, bsB, cB, out1, bsO));
+    }
     PV_CUDA(right3_head(E, bsE, cT2, cB2, T, bsT, cT, a, 0));
     PV_CUDA(right3_tail(a, cT, cB2, B, bsB, cB, out0, bsO));
     PV_CUDA(right3_head(E, bsE, cT2, cB2, T, bsT, cT, a, 1, false));
@@ -625,6 +796,8 @@ struct pepsvmc_ctx {
   cudaError_t left4(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
                     const SiteOp& a1, int f1, const SiteOp& a2, int f2, const float* B, long long bsB, int cB2,
                     float* out, long long bsO) {
+    const Env4Fused f = fused4_left(E, bsE, cT, cB, T, bsT, cT2, a1, f1, a2, f2, B, bsB, cB2, out, bsO);
+    if (fused4_ok(f)) return fused4(f);
     PV_CUDA(left4_x(E, bsE, cT, cB, T, bsT, cT2, a1, a2, tmp1));
     PV_CUDA(left4_y(tmp1, cB, cT2, a1, f1, a2, tmp2));
     return left4_zw(tmp2, cB, cT2, a1, a2, f2, B, bsB, cB2, out, bsO, tmp1);
@@ -678,6 +851,8 @@ struct pepsvmc_ctx {
   cudaError_t right4(const float* E, long long bsE, int cT2, int cB2, const float* T, long long bsT, int cT,
                      const SiteOp& a1, int f1, const SiteOp& a2, int f2, const float* B, long long bsB, int cB,
                      float* out, long long bsO) {
+    const Env4Fused f = fused4_right(E, bsE, cT2, cB2, T, bsT, cT, a1, f1, a2, f2, B, bsB, cB, out, bsO);
+    if (fused4_ok(f)) return fused4(f);
     const int D1l = a1.Dl, D1r = a1.Dr, Du1 = a1.Du, Dd1 = a1.Dd;
     const int D2l = a2.Dl, D2r = a2.Dr, Dd2 = a2.Dd;
     GemmDesc g;
@@ -874,7 +1049,7 @@ struct pepsvmc_ctx {
         ma.n = tb[m + 1] * a[m].Dr * bb[m + 1];
         ma.spins = spins; ma.spin_stride = (long long)Ly * Lx;
         ma.site_a = a[m].spin; ma.site_b = a[m + 1].spin;
-        ma.key = cfg.seed; ma.sweep = d_sweep;
+        ma.key = cfg.seed; ma.sweep = d_sweep; ma.chain_base = chain_base;
         ma.bond = bond_base + k * (Lxo - 1) + m;
         ma.out = l3[0]; ma.bs_out = S;
         ma.trace_ratio = trace_on ? trace_ratio : nullptr;
@@ -1031,7 +1206,7 @@ struct pepsvmc_ctx {
         float* cur = l3[(m + 1) % 2];
         const int n = tb[m + 1] * a[m].Dr * bb[m + 1];
         PV_CUDA(left3_pair(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a[m], B.site(m),
-                           B.chain_stride, bb[m + 1], cur, edge ? nullptr : fl, S));
+                           B.chain_stride, bb[m + 1], cur, edge ? nullptr : fl, S, true));
         PV_CUDA(dot(cur, S, Rin, bsR, n, den));
         if (!edge)
           PV_CUDA(ratio(fl, S, envRfp(m + 1), S, n, a[m].spin, a[m + 1].spin, 0.5 * cfg.J1, (long long)k * Lx + m));
@@ -1087,20 +1262,28 @@ struct pepsvmc_ctx {
         return left4_zw(Y, bb[m], tb[m + 1], a1[m], a2[m], f2, B.site(m), B.chain_stride, bb[m + 1], out, S4,
                         tmp1);
       };
-      PV_CUDA(left4_x(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a1[m], a2[m], tmp1));
-      PV_CUDA(left4_y(tmp1, bb[m], tb[m + 1], a1[m], 0, a2[m], tmp3));
-      PV_CUDA(left4_y(tmp1, bb[m], tb[m + 1], a1[m], 1, a2[m], tmp4));
-      PV_CUDA(from_y(tmp3, 0, cur));
+      // with the fused kernel every variant is one launch from Lin; otherwise the four
+      // variants share X = Lin . T and Y(f1) = X . a1
+      const bool fz = fused4_ok(fused4_left(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a1[m], 0,
+                                            a2[m], 0, B.site(m), B.chain_stride, bb[m + 1], cur, S4));
+      if (fz) {
+        PV_CUDA(step(Lin, bsL, 0, 0, cur));
+      } else {
+        PV_CUDA(left4_x(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a1[m], a2[m], tmp1));
+        PV_CUDA(left4_y(tmp1, bb[m], tb[m + 1], a1[m], 0, a2[m], tmp3));
+        PV_CUDA(left4_y(tmp1, bb[m], tb[m + 1], a1[m], 1, a2[m], tmp4));
+        PV_CUDA(from_y(tmp3, 0, cur));
+      }
       PV_CUDA(dot(cur, S4, Rin, bsR, n, den));
-      PV_CUDA(from_y(tmp4, 1, fl4));
+      PV_CUDA(fz ? step(Lin, bsL, 1, 1, fl4) : from_y(tmp4, 1, fl4));
       PV_CUDA(ratio(fl4, S4, Rin, bsR, n, a1[m].spin, a2[m].spin, 0.5 * cfg.J1, (long long)Ly * Lx + k * Lx + m));
       float *Ptn = nullptr, *Pbn = nullptr;
       if (cfg.J2 != 0.0) {
         if (!edge) {
           Ptn = ptop[(m + 1) % 2];
           Pbn = pbot[(m + 1) % 2];
-          PV_CUDA(from_y(tmp4, 0, Ptn));
-          PV_CUDA(from_y(tmp3, 1, Pbn));
+          PV_CUDA(fz ? step(Lin, bsL, 1, 0, Ptn) : from_y(tmp4, 0, Ptn));
+          PV_CUDA(fz ? step(Lin, bsL, 0, 1, Pbn) : from_y(tmp3, 1, Pbn));
         }
         if (m >= 1) {
           PV_CUDA(step(Pt, S4, 0, 1, fl4));
@@ -1207,7 +1390,7 @@ struct pepsvmc_ctx {
       const View B = view(st_bot, Ly - 2 - k, Ly - 2 - k);
       launches += 8;
       PV_CUDA(net_forward(w, spins, C, Ly, Lx, h1, h2, logits, st));
-      PV_CUDA(propose_moves(logits, spins, prop, C, Ly, Lx, k, cfg.seed, d_sweep, move, lq_fwd, st));
+      PV_CUDA(propose_moves(logits, spins, prop, C, Ly, Lx, k, cfg.seed, d_sweep, move, lq_fwd, chain_base, st));
       PV_CUDA(net_forward(w, prop, C, Ly, Lx, h1, h2, logits2, st));
       PV_CUDA(reverse_logq(logits2, prop, C, Ly, Lx, k, move, lq_rev, st));
       float *den_p = nullptr, *num_p = nullptr;
@@ -1216,7 +1399,7 @@ struct pepsvmc_ctx {
       ++launches;
       PV_CUDA(accept_moves(spins, prop, C, (int)N, move, den_p, num_p, S4, ex_den, ex_num, lq_fwd, lq_rev, cfg.seed,
                            d_sweep, k, Ly - 1, trace_on ? ltr_rho : nullptr, ltr_dlq, trace_on ? ltr_dec : nullptr,
-                           lcount, status, st));
+                           lcount, status, chain_base, st));
       PV_CUDA(compress(0, k, T, st_top, k + 1, k + 1));
     }
     top_valid = true;
@@ -1334,7 +1517,9 @@ int validate(const pepsvmc_config* c, std::string& why) {
     why = "unknown precision";
     return PEPSVMC_EINVAL;
   }
-  for (int i = 0; i < 6; ++i)
+  if (c->chain_offset < 0) { why = "chain_offset must be >= 0"; return PEPSVMC_EINVAL; }
+  if (c->wait_budget_cycles > (uint64_t)1 << 62) { why = "wait_budget_cycles too large"; return PEPSVMC_EINVAL; }
+  for (int i = 0; i < 3; ++i)
     if (c->reserved[i]) { why = "reserved fields must be zero"; return PEPSVMC_EINVAL; }
   return PEPSVMC_OK;
 }
@@ -1532,6 +1717,8 @@ int pepsvmc_init(const pepsvmc_config* cfg, const double* tensors, const double*
   x->chi_m = cfg->chi_measure ? cfg->chi_measure : cfg->chi;
   x->chi_x = std::max(x->chi_s, x->chi_m);
   x->nfit = cfg->n_fit;
+  x->wait_budget = (long long)cfg->wait_budget_cycles;
+  x->chain_base = (unsigned)cfg->chain_offset;
   return setup(x, tensors, sketch);
 }
 
@@ -1565,10 +1752,92 @@ int pepsvmc_env3_left(pepsvmc_ctx* x, const float* E, const float* T, const floa
     return x->fail(PEPSVMC_EINVAL, "env3_left: null pointer or non-positive size");
   if (n_chains > x->C || env3_scratch(d) > x->SI)
     return x->fail(PEPSVMC_EINVAL, "env3_left: more chains or larger bonds than the context was created for");
+  SiteOp op;
+  op.Dl = Dl; op.Dr = Dr; op.Du = Du; op.Dd = Dd;
+  op.size = (long long)Dl * Dr * Du * Dd;
+  op.lurd = A;
+  op.spin = 0;
+  if (x->fused_ok(cT, cB, cT2, cB2, op)) {
+    Env3Fused f = x->fused_left(E, (long long)cT * Dl * cB, cT, cB, T, (long long)cT * Du * cT2, cT2, op, 0, B,
+                                (long long)cB * Dd * cB2, cB2, out, (long long)cT2 * Dr * cB2);
+    f.sel = spins;
+    f.sel_stride = 1;
+    cudaError_t e = x->fused3(f, n_chains, true);
+    return e == cudaSuccess ? PEPSVMC_OK : x->fail_cuda(e);
+  }
   GemmDesc g[3];
   env3_left_descs(g, d, E, (long long)cT * Dl * cB, T, (long long)cT * Du * cT2, A, (long long)Dl * Dr * Du * Dd,
                   spins, 1, 0, B, (long long)cB * Dd * cB2, out, (long long)cT2 * Dr * cB2, x->tmp1, x->tmp2, x->SI);
   for (int i = 0; i < 3; ++i) {
+    g[i].batch = n_chains;
+    ++x->launches;
+    cudaError_t e = x->launch_gemm(g[i]);
+    if (e != cudaSuccess) return x->fail_cuda(e);
+  }
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_env4_left(pepsvmc_ctx* x, const float* E, const float* T, const float* A1, const int8_t* spins1,
+                      const float* A2, const int8_t* spins2, const float* B, float* out, int32_t n_chains, int32_t cT,
+                      int32_t cB, int32_t cT2, int32_t cB2, int32_t D1l, int32_t D1r, int32_t Du1, int32_t Dd1,
+                      int32_t D2l, int32_t D2r, int32_t Dd2) {
+  if (!x) return PEPSVMC_EINVAL;
+  const int dims[11] = {cT, cB, cT2, cB2, D1l, D1r, Du1, Dd1, D2l, D2r, Dd2};
+  if (!E || !T || !A1 || !A2 || !B || !out || n_chains < 1)
+    return x->fail(PEPSVMC_EINVAL, "env4_left: null pointer or no chains");
+  for (int v : dims)
+    if (v < 1) return x->fail(PEPSVMC_EINVAL, "env4_left: non-positive size");
+  const long long X = (long long)D2l * cB * cT2 * std::max(D1l * Du1, D1r * Dd1);
+  const long long Z = (long long)cB * cT2 * D1r * std::max(D2l * Dd1, D2r * Dd2);
+  if (n_chains > x->C || std::max(X, Z) > x->SI)
+    return x->fail(PEPSVMC_EINVAL, "env4_left: more chains or larger bonds than the context was created for");
+  const long long s1 = (long long)D1l * Du1 * D1r * Dd1, s2 = (long long)D2l * Dd1 * D2r * Dd2;
+  Env4Fused f;
+  f.cT = cT; f.cB = cB; f.cT2 = cT2; f.cB2 = cB2;
+  f.D1l = D1l; f.D1r = D1r; f.Du1 = Du1; f.Dd1 = Dd1; f.D2l = D2l; f.D2r = D2r; f.Dd2 = Dd2;
+  if (x->fused4_ok(f)) {
+    f.batch = n_chains;
+    f.wait_cycles = x->wait_budget;
+    f.E = E; f.bsE = (long long)cT * D1l * D2l * cB; f.sEa = (long long)D1l * D2l * cB; f.sEl1 = (long long)D2l * cB;
+    f.sEl2 = cB; f.sEb = 1;
+    f.T = T; f.bsT = (long long)cT * Du1 * cT2; f.sTa = (long long)Du1 * cT2; f.sTu = cT2; f.sTa2 = 1;
+    f.A1 = A1; f.ss1 = s1; f.s1l = (long long)Du1 * D1r * Dd1; f.s1u = (long long)D1r * Dd1; f.s1r = Dd1; f.s1d = 1;
+    f.A2 = A2; f.ss2 = s2; f.s2l = (long long)Dd1 * D2r * Dd2; f.s2u = (long long)D2r * Dd2; f.s2r = Dd2; f.s2d = 1;
+    f.sel1 = spins1; f.sel2 = spins2; f.sel_stride = 1;
+    f.B = B; f.bsB = (long long)cB * Dd2 * cB2; f.sBb = (long long)Dd2 * cB2; f.sBd = cB2; f.sBb2 = 1;
+    f.out = out; f.bsO = (long long)cT2 * D1r * D2r * cB2; f.sOa2 = (long long)D1r * D2r * cB2;
+    f.sOr1 = (long long)D2r * cB2; f.sOr2 = cB2; f.sOb2 = 1;
+    ++x->launches;
+    cudaError_t e = env4_fused(f, x->tc_mode() == 3, x->status, x->st);
+    return e == cudaSuccess ? PEPSVMC_OK : x->fail_cuda(e);
+  }
+  // four separate products, as left4_x / left4_y / left4_zw with the caller's spins
+  GemmDesc g[4];
+  float* t1 = x->tmp1;
+  float* t2 = x->tmp2;
+  g[0].M = D1l * D2l * cB; g[0].N = Du1 * cT2; g[0].K = cT;
+  g[0].A = E; g[0].sAm = 1; g[0].sAk = (long long)D1l * D2l * cB; g[0].bsA = (long long)cT * D1l * D2l * cB;
+  g[0].B = T; g[0].sBk = (long long)Du1 * cT2; g[0].sBn = 1; g[0].bsB = (long long)cT * Du1 * cT2;
+  g[0].C = t1; g[0].bsC = x->SI;
+  g[0].cm2 = D2l * cB; g[0].sCm1 = Du1; g[0].sCm2 = (long long)cT2 * D1l * Du1;
+  g[0].cn2 = cT2; g[0].sCn1 = 1; g[0].sCn2 = (long long)D1l * Du1;
+  g[1].M = D2l * cB * cT2; g[1].N = D1r * Dd1; g[1].K = D1l * Du1;
+  g[1].A = t1; g[1].sAm = (long long)D1l * Du1; g[1].sAk = 1; g[1].bsA = x->SI;
+  g[1].B = A1; g[1].ssB = s1; g[1].sel = spins1; g[1].sel_stride = 1; g[1].sBk = (long long)D1r * Dd1; g[1].sBn = 1;
+  g[1].C = t2; g[1].bsC = x->SI;
+  g[1].cm2 = cB * cT2; g[1].sCm1 = Dd1; g[1].sCm2 = (long long)D1r * D2l * Dd1;
+  g[1].cn2 = Dd1; g[1].sCn1 = (long long)D2l * Dd1; g[1].sCn2 = 1;
+  g[2].M = cB * cT2 * D1r; g[2].N = D2r * Dd2; g[2].K = D2l * Dd1;
+  g[2].A = t2; g[2].sAm = (long long)D2l * Dd1; g[2].sAk = 1; g[2].bsA = x->SI;
+  g[2].B = A2; g[2].ssB = s2; g[2].sel = spins2; g[2].sel_stride = 1; g[2].sBk = (long long)D2r * Dd2; g[2].sBn = 1;
+  g[2].C = t1; g[2].bsC = x->SI;
+  g[2].cm2 = cT2 * D1r; g[2].sCm1 = Dd2; g[2].sCm2 = (long long)D2r * cB * Dd2;
+  g[2].cn2 = Dd2; g[2].sCn1 = (long long)cB * Dd2; g[2].sCn2 = 1;
+  g[3].M = cT2 * D1r * D2r; g[3].N = cB2; g[3].K = cB * Dd2;
+  g[3].A = t1; g[3].sAm = (long long)cB * Dd2; g[3].sAk = 1; g[3].bsA = x->SI;
+  g[3].B = B; g[3].sBk = cB2; g[3].sBn = 1; g[3].bsB = (long long)cB * Dd2 * cB2;
+  g[3].C = out; g[3].bsC = (long long)cT2 * D1r * D2r * cB2; g[3].sCm1 = cB2; g[3].sCn1 = 1;
+  for (int i = 0; i < 4; ++i) {
     g[i].batch = n_chains;
     ++x->launches;
     cudaError_t e = x->launch_gemm(g[i]);
@@ -1997,6 +2266,62 @@ int pepsvmc_energy_and_grad(pepsvmc_ctx* x, int32_t n, double* E_mean, double* E
   if (E_mean) *E_mean = mean;
   if (E_var) *E_var = s[1] / s[2] - mean * mean;
   if (grad && (e = x->cps(grad, x->grad, x->P * sizeof(double), cudaMemcpyDeviceToHost))) return x->fail_cuda(e);
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_set_fused(pepsvmc_ctx* x, int32_t on) {
+  if (!x) return PEPSVMC_EINVAL;
+  x->fused_on = on != 0;
+  x->drop_graph();
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_set_wait_budget(pepsvmc_ctx* x, uint64_t cycles) {
+  if (!x) return PEPSVMC_EINVAL;
+  if (cycles > (uint64_t)1 << 62) return x->fail(PEPSVMC_EINVAL, "wait budget too large");
+  x->wait_budget = (long long)cycles;
+  x->drop_graph();  // a captured step carries the old budget in its launch arguments
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_get_sums(pepsvmc_ctx* x, double* scalars, double* sumGE, double* sumG) {
+  if (!x || !scalars) return PEPSVMC_EINVAL;
+  if (!x->have_grad) return x->fail(PEPSVMC_ESTATE, "no sums: call pepsvmc_energy_and_grad first");
+  cudaError_t e = x->cp(scalars, x->sums, 3 * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && sumGE) e = x->cp(sumGE, x->sumGE, x->P * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && sumG) e = x->cp(sumG, x->sumG, x->P * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = x->sync();
+  return e == cudaSuccess ? PEPSVMC_OK : x->fail_cuda(e);
+}
+
+int pepsvmc_finalize_sums(pepsvmc_ctx* x) {
+  if (!x) return PEPSVMC_EINVAL;
+  double n = 0.0;
+  cudaError_t e = x->cps(&n, x->sums + 2, sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  if (!x->dry && !(n > 0.0)) return x->fail(PEPSVMC_EINVAL, "sums: the sample count must be positive");
+  ++x->launches;
+  if ((e = k_grad_final(x->sumG, x->sumGE, x->sums, x->P, x->grad, x->st)) != cudaSuccess) return x->fail_cuda(e);
+  if ((e = x->sync()) != cudaSuccess) return x->fail_cuda(e);
+  x->have_grad = true;
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_set_sums(pepsvmc_ctx* x, const double* scalars, const double* sumGE, const double* sumG) {
+  if (!x || !scalars || !sumGE || !sumG) return PEPSVMC_EINVAL;
+  if (!(scalars[2] > 0.0)) return x->fail(PEPSVMC_EINVAL, "sums: the sample count must be positive");
+  cudaError_t e = x->cp(x->sums, scalars, 3 * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = x->cp(x->sumGE, sumGE, x->P * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = x->cp(x->sumG, sumG, x->P * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  return pepsvmc_finalize_sums(x);
+}
+
+int pepsvmc_sums_device(pepsvmc_ctx* x, double** scalars, double** sumGE, double** sumG) {
+  if (!x || !scalars || !sumGE || !sumG) return PEPSVMC_EINVAL;
+  *scalars = x->sums;
+  *sumGE = x->sumGE;
+  *sumG = x->sumG;
   return PEPSVMC_OK;
 }
 

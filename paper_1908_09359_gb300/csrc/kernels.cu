@@ -153,7 +153,7 @@ __global__ void metropolis_kernel(const MetropolisArgs a) {
           atomicOr(a.status, ST_NONFINITE);
         } else {
           const uint4 w = philox4x32_10(
-              make_uint4((unsigned)b, (unsigned)*a.sweep, (unsigned)a.bond, kTagMetropolis),
+              make_uint4((unsigned)b + a.chain_base, (unsigned)*a.sweep, (unsigned)a.bond, kTagMetropolis),
               make_uint2((unsigned)(a.key & 0xffffffffull), (unsigned)(a.key >> 32)));
           const double u = uniform24(w.x);
           const double p = fmin(1.0, rho * rho);

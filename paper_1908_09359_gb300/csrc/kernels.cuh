@@ -16,6 +16,7 @@ struct MetropolisArgs {
   int8_t* spins; long long spin_stride;
   int site_a, site_b;                    // original lattice indices k*Lx+m of the pair
   unsigned long long key;                // Philox key (seed)
+  unsigned chain_base;                   // global index of chain 0 (Philox counter word 0)
   const unsigned long long* sweep;       // device-resident sweep counter (read at run time)
   int bond;
   float* out; long long bs_out;          // selected, normalised L(m)

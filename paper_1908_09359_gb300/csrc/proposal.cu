@@ -237,7 +237,8 @@ __device__ int find(const Cand* c, int n, int a, int b) {
 }
 
 __global__ void propose_kernel(const float* logits, const int8_t* spins, int8_t* prop, int C, int Ly, int Lx, int k,
-                               unsigned long long key, const unsigned long long* sweep, int* move, double* lq) {
+                               unsigned long long key, const unsigned long long* sweep, int* move, double* lq,
+                               unsigned chain_base) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   const int N = Ly * Lx;
@@ -251,7 +252,8 @@ __global__ void propose_kernel(const float* logits, const int8_t* spins, int8_t*
   const int n = band_candidates(s, logits + (long long)c * 2 * N, Ly, Lx, k, cand);
   if (n == 0) return;
   const unsigned sw = (unsigned)*sweep;
-  const double u0 = uni(key, c, sw, 4 * k), u1 = uni(key, c, sw, 4 * k + 1), u2 = uni(key, c, sw, 4 * k + 2);
+  const unsigned cg = (unsigned)c + chain_base;
+  const double u0 = uni(key, cg, sw, 4 * k), u1 = uni(key, cg, sw, 4 * k + 1), u2 = uni(key, cg, sw, 4 * k + 2);
   bool use[kMaxCand];
   for (int t = 0; t < n; ++t) use[t] = true;
   const int i = soft_draw(cand, n, use, u1);
@@ -296,7 +298,7 @@ __global__ void accept_kernel(int8_t* spins, const int8_t* prop, int C, int N, c
                               const float* num, long long bs, const int* e_den, const int* e_num,
                               const double* lq_fwd, const double* lq_rev, unsigned long long key,
                               const unsigned long long* sweep, int k, int Lb, double* tr_rho, double* tr_dlq,
-                              int8_t* tr_dec, unsigned long long* counters, unsigned* status) {
+                              int8_t* tr_dec, unsigned long long* counters, unsigned* status, unsigned chain_base) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   int dec = -1;
@@ -310,7 +312,7 @@ __global__ void accept_kernel(int8_t* spins, const int8_t* prop, int C, int N, c
       dlq = lq_rev[c] - lq_fwd[c];
       const double a = fmin(1.0, rho * rho * exp(dlq));
       if (!isfinite(a)) atomicOr(status, ST_NONFINITE);
-      dec = (uni(key, c, (unsigned)*sweep, 4 * k + 3) < a) ? 1 : 0;
+      dec = (uni(key, (unsigned)c + chain_base, (unsigned)*sweep, 4 * k + 3) < a) ? 1 : 0;
       atomicAdd(&counters[0], 1ull);
       if (dec) {
         atomicAdd(&counters[1], 1ull);
@@ -368,9 +370,10 @@ cudaError_t net_train_step(const NetParams& w, const NetParams& g, float* m, flo
 
 cudaError_t propose_moves(const float* logits, const int8_t* spins, int8_t* prop, int C, int Ly, int Lx, int k,
                           unsigned long long key, const unsigned long long* sweep, int* move, double* lq,
-                          cudaStream_t st) {
+                          unsigned chain_base, cudaStream_t st) {
   if (g_dry_run) return cudaSuccess;
-  propose_kernel<<<(C + 127) / 128, 128, 0, st>>>(logits, spins, prop, C, Ly, Lx, k, key, sweep, move, lq);
+  propose_kernel<<<(C + 127) / 128, 128, 0, st>>>(logits, spins, prop, C, Ly, Lx, k, key, sweep, move, lq,
+                                                  chain_base);
   return cudaGetLastError();
 }
 
@@ -385,10 +388,11 @@ cudaError_t accept_moves(int8_t* spins, const int8_t* prop, int C, int N, const 
                          const float* num, long long bs, const int* e_den, const int* e_num, const double* lq_fwd,
                          const double* lq_rev, unsigned long long key, const unsigned long long* sweep, int k,
                          int Lb, double* tr_rho, double* tr_dlq, int8_t* tr_dec, unsigned long long* counters,
-                         unsigned* status, cudaStream_t st) {
+                         unsigned* status, unsigned chain_base, cudaStream_t st) {
   if (g_dry_run) return cudaSuccess;
   accept_kernel<<<(C + 127) / 128, 128, 0, st>>>(spins, prop, C, N, move, den, num, bs, e_den, e_num, lq_fwd, lq_rev,
-                                                 key, sweep, k, Lb, tr_rho, tr_dlq, tr_dec, counters, status);
+                                                 key, sweep, k, Lb, tr_rho, tr_dlq, tr_dec, counters, status,
+                                                 chain_base);
   return cudaGetLastError();
 }
 

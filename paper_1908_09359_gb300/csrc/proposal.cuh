@@ -35,7 +35,7 @@ cudaError_t net_train_step(const NetParams& w, const NetParams& g, float* m, flo
 // (-1: none), lq = ln q(S'|S).
 cudaError_t propose_moves(const float* logits, const int8_t* spins, int8_t* prop, int C, int Ly, int Lx, int k,
                           unsigned long long key, const unsigned long long* sweep, int* move, double* lq,
-                          cudaStream_t st);
+                          unsigned chain_base, cudaStream_t st);
 // lq_rev = ln q(S|S') from the logits of S'.
 cudaError_t reverse_logq(const float* logits, const int8_t* prop, int C, int Ly, int Lx, int k, const int* move,
                          double* lq_rev, cudaStream_t st);
@@ -45,6 +45,6 @@ cudaError_t accept_moves(int8_t* spins, const int8_t* prop, int C, int N, const 
                          const float* num, long long bs, const int* e_den, const int* e_num, const double* lq_fwd,
                          const double* lq_rev, unsigned long long key, const unsigned long long* sweep, int k,
                          int Lb, double* tr_rho, double* tr_dlq, int8_t* tr_dec, unsigned long long* counters,
-                         unsigned* status, cudaStream_t st);
+                         unsigned* status, unsigned chain_base, cudaStream_t st);
 
 }  // namespace pv

@@ -4,7 +4,9 @@ With PEPSVMC_DRY_RUN=1 the library skips every device call but still walks the w
 orchestration -- boundary-MPS fits in four lattice orientations, both sweep phases,
 the three- and four-line measurement, gradient accumulation and sign-SGD -- and
 checks the memory span of every launch against its allocation.  This runs each
-workload's full launch sequence in a subprocess (the mode is process-wide).
+workload's full launch sequence in a subprocess (the mode is process-wide), in FP32
+(separate products) and in split BF16 (fused three- and four-line steps where the bonds
+fit, separate tensor-core products elsewhere).
 """
 import json
 import os
@@ -29,7 +31,7 @@ chi_s = max(1, (2 * w["chi"]) // 3) if sys.argv[2] == "split" else w["chi"]
 chi_m = w["chi"] if sys.argv[2] == "split" else 0
 sk = np.zeros((L, w["chi"], w["D"], w["chi"]))
 c = api.PepsVMC(w["Ly"], w["Lx"], w["D"], chi_s, w["n_chains"], t, sk, J1=w["J1"], J2=w["J2"],
-                seed=1, n_fit=3, stream=0, chi_measure=chi_m)
+                seed=1, n_fit=3, stream=0, chi_measure=chi_m, precision=int(sys.argv[3]))
 n0 = c.launches
 c.sample_sweep(1)
 n1 = c.launches
@@ -50,13 +52,14 @@ print(json.dumps(dict(sweep=n1 - n0, measure=n2 - n1)))
 """
 
 
+@pytest.mark.parametrize("precision", [0, 3])
 @pytest.mark.parametrize("cutoffs", ["one", "split"])
 @pytest.mark.parametrize("name", list(inputs.WORKLOADS))
-def test_every_launch_in_bounds(name, cutoffs):
+def test_every_launch_in_bounds(name, cutoffs, precision):
     build.build()
     env = dict(os.environ, PEPSVMC_DRY_RUN="1", PYTHONPATH=ROOT)
-    r = subprocess.run([sys.executable, "-c", SCRIPT, name, cutoffs], capture_output=True, text=True, env=env,
-                       timeout=600, cwd=ROOT)
+    r = subprocess.run([sys.executable, "-c", SCRIPT, name, cutoffs, str(precision)], capture_output=True,
+                       text=True, env=env, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     counts = json.loads(r.stdout.strip().splitlines()[-1])
     assert counts["sweep"] > 0 and counts["measure"] > 0
