@@ -572,6 +572,14 @@ struct pepsvmc_ctx {
   bool fused4_ok(const Env4Fused& f) const {
     return fused_on && forced < 0 && (tc_mode() == 2 || tc_mode() == 3) && env4_fused_fits(f);
   }
+  // Every four-line step of this context runs fused (all bonds within the kernel's
+  // maxima): the four-line environments are then stored b-major, E(a,l1,l2,b) at
+  // [b][a][l1][l2], so that the kernel's slices of consecutive b are contiguous.  The
+  // consumers of these environments (dot, ratio, normalisation) are element-wise over
+  // matching layouts, so only the fused steps see the order.
+  bool four_bmajor() const {
+    return fused_on && forced < 0 && (tc_mode() == 2 || tc_mode() == 3) && chi_x <= kFusedChi && D <= kFusedD;
+  }
   // left step of rows (k,k+1): E (cT,D1l,D2l,cB), T (cT,Du1,cT2), B (cB,Dd2,cB2) -> out (cT2,D1r,D2r,cB2)
   Env4Fused fused4_left(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
                         const SiteOp& a1, int f1, const SiteOp& a2, int f2, const float* B, long long bsB, int cB2,
@@ -579,7 +587,12 @@ struct pepsvmc_ctx {
     Env4Fused f;
     f.cT = cT; f.cB = cB; f.cT2 = cT2; f.cB2 = cB2;
     f.D1l = a1.Dl; f.D1r = a1.Dr; f.Du1 = a1.Du; f.Dd1 = a1.Dd; f.D2l = a2.Dl; f.D2r = a2.Dr; f.Dd2 = a2.Dd;
-    f.E = E; f.bsE = bsE; f.sEa = (long long)a1.Dl * a2.Dl * cB; f.sEl1 = (long long)a2.Dl * cB; f.sEl2 = cB; f.sEb = 1;
+    f.E = E; f.bsE = bsE;
+    if (four_bmajor()) {
+      f.sEb = (long long)cT * a1.Dl * a2.Dl; f.sEa = (long long)a1.Dl * a2.Dl; f.sEl1 = a2.Dl; f.sEl2 = 1;
+    } else {
+      f.sEa = (long long)a1.Dl * a2.Dl * cB; f.sEl1 = (long long)a2.Dl * cB; f.sEl2 = cB; f.sEb = 1;
+    }
     f.T = T; f.bsT = bsT; f.sTa = (long long)a1.Du * cT2; f.sTu = cT2; f.sTa2 = 1;
     f.A1 = a1.lurd; f.ss1 = a1.size;
     f.s1l = (long long)a1.Du * a1.Dr * a1.Dd; f.s1u = (long long)a1.Dr * a1.Dd; f.s1r = a1.Dd; f.s1d = 1;
@@ -588,8 +601,12 @@ struct pepsvmc_ctx {
     const int8_t* sb = sel_base ? sel_base : spins;
     f.sel1 = sb + a1.spin; f.sel2 = sb + a2.spin; f.sel_stride = (long long)Ly * Lx; f.xor1 = f1; f.xor2 = f2;
     f.B = B; f.bsB = bsB; f.sBb = (long long)a2.Dd * cB2; f.sBd = cB2; f.sBb2 = 1;
-    f.out = out; f.bsO = bsO; f.sOa2 = (long long)a1.Dr * a2.Dr * cB2; f.sOr1 = (long long)a2.Dr * cB2; f.sOr2 = cB2;
-    f.sOb2 = 1;
+    f.out = out; f.bsO = bsO;
+    if (four_bmajor()) {
+      f.sOb2 = (long long)cT2 * a1.Dr * a2.Dr; f.sOa2 = (long long)a1.Dr * a2.Dr; f.sOr1 = a2.Dr; f.sOr2 = 1;
+    } else {
+      f.sOa2 = (long long)a1.Dr * a2.Dr * cB2; f.sOr1 = (long long)a2.Dr * cB2; f.sOr2 = cB2; f.sOb2 = 1;
+    }
     return f;
   }
   // right step as a mirrored left step: E (cT2,D1r,D2r,cB2) -> out (cT,D1l,D2l,cB)
@@ -599,8 +616,12 @@ struct pepsvmc_ctx {
     Env4Fused f;
     f.cT = cT2; f.cB = cB2; f.cT2 = cT; f.cB2 = cB;
     f.D1l = a1.Dr; f.D1r = a1.Dl; f.Du1 = a1.Du; f.Dd1 = a1.Dd; f.D2l = a2.Dr; f.D2r = a2.Dl; f.Dd2 = a2.Dd;
-    f.E = E; f.bsE = bsE; f.sEa = (long long)a1.Dr * a2.Dr * cB2; f.sEl1 = (long long)a2.Dr * cB2; f.sEl2 = cB2;
-    f.sEb = 1;
+    f.E = E; f.bsE = bsE;
+    if (four_bmajor()) {
+      f.sEb = (long long)cT2 * a1.Dr * a2.Dr; f.sEa = (long long)a1.Dr * a2.Dr; f.sEl1 = a2.Dr; f.sEl2 = 1;
+    } else {
+      f.sEa = (long long)a1.Dr * a2.Dr * cB2; f.sEl1 = (long long)a2.Dr * cB2; f.sEl2 = cB2; f.sEb = 1;
+    }
     f.T = T; f.bsT = bsT; f.sTa = 1; f.sTu = cT2; f.sTa2 = (long long)a1.Du * cT2;
     f.A1 = a1.lurd; f.ss1 = a1.size;
     f.s1l = a1.Dd; f.s1u = (long long)a1.Dr * a1.Dd; f.s1r = (long long)a1.Du * a1.Dr * a1.Dd; f.s1d = 1;
@@ -609,8 +630,12 @@ struct pepsvmc_ctx {
     const int8_t* sb = sel_base ? sel_base : spins;
     f.sel1 = sb + a1.spin; f.sel2 = sb + a2.spin; f.sel_stride = (long long)Ly * Lx; f.xor1 = f1; f.xor2 = f2;
     f.B = B; f.bsB = bsB; f.sBb = 1; f.sBd = cB2; f.sBb2 = (long long)a2.Dd * cB2;
-    f.out = out; f.bsO = bsO; f.sOa2 = (long long)a1.Dl * a2.Dl * cB; f.sOr1 = (long long)a2.Dl * cB; f.sOr2 = cB;
-    f.sOb2 = 1;
+    f.out = out; f.bsO = bsO;
+    if (four_bmajor()) {
+      f.sOb2 = (long long)cT * a1.Dl * a2.Dl; f.sOa2 = (long long)a1.Dl * a2.Dl; f.sOr1 = a2.Dl; f.sOr2 = 1;
+    } else {
+      f.sOa2 = (long long)a1.Dl * a2.Dl * cB; f.sOr1 = (long long)a2.Dl * cB; f.sOr2 = cB; f.sOb2 = 1;
+    }
     return f;
   }
 
@@ -796,8 +821,8 @@ struct pepsvmc_ctx {
   cudaError_t left4(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
                     const SiteOp& a1, int f1, const SiteOp& a2, int f2, const float* B, long long bsB, int cB2,
                     float* out, long long bsO) {
-    const Env4Fused f = fused4_left(E, bsE, cT, cB, T, bsT, cT2, a1, f1, a2, f2, B, bsB, cB2, out, bsO);
-    if (fused4_ok(f)) return fused4(f);
+    if (four_bmajor())
+      return fused4(fused4_left(E, bsE, cT, cB, T, bsT, cT2, a1, f1, a2, f2, B, bsB, cB2, out, bsO));
     PV_CUDA(left4_x(E, bsE, cT, cB, T, bsT, cT2, a1, a2, tmp1));
     PV_CUDA(left4_y(tmp1, cB, cT2, a1, f1, a2, tmp2));
     return left4_zw(tmp2, cB, cT2, a1, a2, f2, B, bsB, cB2, out, bsO, tmp1);
@@ -851,8 +876,8 @@ struct pepsvmc_ctx {
   cudaError_t right4(const float* E, long long bsE, int cT2, int cB2, const float* T, long long bsT, int cT,
                      const SiteOp& a1, int f1, const SiteOp& a2, int f2, const float* B, long long bsB, int cB,
                      float* out, long long bsO) {
-    const Env4Fused f = fused4_right(E, bsE, cT2, cB2, T, bsT, cT, a1, f1, a2, f2, B, bsB, cB, out, bsO);
-    if (fused4_ok(f)) return fused4(f);
+    if (four_bmajor())
+      return fused4(fused4_right(E, bsE, cT2, cB2, T, bsT, cT, a1, f1, a2, f2, B, bsB, cB, out, bsO));
     const int D1l = a1.Dl, D1r = a1.Dr, Du1 = a1.Du, Dd1 = a1.Dd;
     const int D2l = a2.Dl, D2r = a2.Dr, Dd2 = a2.Dd;
     GemmDesc g;
@@ -1264,8 +1289,7 @@ struct pepsvmc_ctx {
       };
       // with the fused kernel every variant is one launch from Lin; otherwise the four
       // variants share X = Lin . T and Y(f1) = X . a1
-      const bool fz = fused4_ok(fused4_left(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a1[m], 0,
-                                            a2[m], 0, B.site(m), B.chain_stride, bb[m + 1], cur, S4));
+      const bool fz = four_bmajor();
       if (fz) {
         PV_CUDA(step(Lin, bsL, 0, 0, cur));
       } else {

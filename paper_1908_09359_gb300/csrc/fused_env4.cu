@@ -12,10 +12,12 @@
 // accumulators are drained after each product by the epilogue warps, split into BF16
 // hi + lo and stored, re-indexed, as the next product's A operand (S2's in the 128-byte
 // swizzled layout, S3's and S4's without swizzle; in every case the eight lanes that write
-// one row group hit eight different bank groups).  The E and B slices of the next b tile
-// are fetched into registers while the current tile computes and stored into the other
-// half of a double buffer.  Bonds below the maxima are zero-padded on chip.  Shared
-// memory 172 KB (one CTA per SM), tensor memory 512 columns (320 used).
+// one row group hit eight different bank groups).  X, Y and Z share one buffer (each is
+// dead once its product completed) and S3 reuses S1's accumulator columns.  The E and B
+// slices of the next b tile are fetched into registers while the current tile computes.
+// Bonds below the maxima are zero-padded on chip.  Shared memory 93 KB and 256 tensor-
+// memory columns per CTA: two CTAs share an SM, so one CTA's epilogues overlap the
+// other's products.
 #include "fused.cuh"
 #include "tc_util.cuh"
 
@@ -28,19 +30,17 @@ constexpr int kThreads = 256;
 constexpr int kAT = 8;  // a' per tile
 constexpr int kBT = 2;  // b per tile
 
-constexpr uint32_t SZ_X = 128 * 128, OFF_X = 0;                   // S2 A, swizzled
-constexpr uint32_t SZ_E = 128 * 64, OFF_E = OFF_X + 2 * SZ_X;       // S1 A, two buffers
-constexpr uint32_t SZ_T = 64 * 64, OFF_T = OFF_E + 4 * SZ_E;        // S1 B
+constexpr uint32_t SZ_W = 128 * 128, OFF_W = 0;                   // X (S2 A, swizzled), Y (S3 A) or Z (S4 A)
+constexpr uint32_t SZ_E = 128 * 64, OFF_E = OFF_W + 2 * SZ_W;       // S1 A
+constexpr uint32_t SZ_T = 64 * 64, OFF_T = OFF_E + 2 * SZ_E;        // S1 B
 constexpr uint32_t SZ_A1 = 64 * 128, OFF_A1 = OFF_T + 2 * SZ_T;     // S2 B
 constexpr uint32_t SZ_A2 = 64 * 128, OFF_A2 = OFF_A1 + 2 * SZ_A1;   // S3 B
-constexpr uint32_t SZ_Y = 128 * 128, OFF_Y = OFF_A2 + 2 * SZ_A2;    // S3 A
-constexpr uint32_t SZ_Z = 512 * 32, OFF_Z = OFF_Y + 2 * SZ_Y;       // S4 A
-constexpr uint32_t SZ_B = 32 * 32, OFF_B = OFF_Z + 2 * SZ_Z;        // S4 B, two buffers
+constexpr uint32_t SZ_B = 32 * 32, OFF_B = OFF_A2 + 2 * SZ_A2;      // S4 B, two buffers
 constexpr uint32_t SMEM_USED = OFF_B + 4 * SZ_B;
 constexpr uint32_t SMEM_BYTES = SMEM_USED + 1024;
-constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t COL_S1 = 0, COL_S2 = 64, COL_S3 = 128, COL_S4 = 192;
-static_assert(SMEM_BYTES <= 232448, "fused four-line step exceeds the shared memory of one CTA");
+constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t COL_S1 = 0, COL_S2 = 64, COL_S3 = 0, COL_S4 = 128;
+static_assert(2 * (SMEM_BYTES + 1024) <= 233472, "two fused four-line CTAs must fit one SM");
 
 __device__ __forceinline__ bool block_wait(uint64_t* bar, uint32_t parity, long long budget) {
   const bool w = wait_parity(bar, parity, budget);
@@ -88,17 +88,20 @@ __device__ __forceinline__ void fetch_slice(const Env4Fused& a, const float* E, 
 }
 
 template <bool X3>
-__device__ __forceinline__ void store_slice(uint8_t* sm, int buf, int tid, const Slice& s) {
+__device__ __forceinline__ void store_e(uint8_t* sm, int tid, const Slice& s) {
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const int u = tid + i * kThreads;
-    put16<2, X3>(sm + OFF_E + buf * 2 * SZ_E + kmajor_off(u & 127, (u >> 7) * 8, 4), s.e[i], SZ_E);
+    put16<2, X3>(sm + OFF_E + kmajor_off(u & 127, (u >> 7) * 8, 4), s.e[i], SZ_E);
   }
+}
+template <bool X3>
+__device__ __forceinline__ void store_b(uint8_t* sm, int buf, int tid, const Slice& s) {
   if (tid < 64) put16<2, X3>(sm + OFF_B + buf * 2 * SZ_B + kmajor_off(tid & 31, (tid >> 5) * 8, 2), s.b, SZ_B);
 }
 
 template <bool X3>
-__global__ void __launch_bounds__(kThreads, 1) env4_fused_kernel(const Env4Fused a, unsigned* status) {
+__global__ void __launch_bounds__(kThreads, 2) env4_fused_kernel(const Env4Fused a, unsigned* status) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bar[4];
   __shared__ uint32_t tmem_base;
@@ -154,7 +157,8 @@ __global__ void __launch_bounds__(kThreads, 1) env4_fused_kernel(const Env4Fused
       put16<2, X3>(sm + OFF_A2 + kmajor_off(rw, l * 8, 8), v, SZ_A2);
     }
   }
-  store_slice<X3>(sm, 0, tid, nxt);
+  store_e<X3>(sm, tid, nxt);
+  store_b<X3>(sm, 0, tid, nxt);
   fence_async_smem();
   tc_before_sync();
   __syncthreads();
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1) env4_fused_kernel(const Env4Fused
       tc_after_sync();
       const uint32_t id = idesc<2>(128, 64);
       for (int ks = 0; ks < 2; ++ks) {
-        const uint32_t ao = sbase + OFF_E + buf * 2 * SZ_E + ks * 256, bo = sbase + OFF_T + ks * 256;
+        const uint32_t ao = sbase + OFF_E + ks * 256, bo = sbase + OFF_T + ks * 256;
         issue3<X3>(tmem + COL_S1, sdesc(ao, 128, 512), sdesc(ao + SZ_E, 128, 512), sdesc(bo, 128, 512),
                    sdesc(bo + SZ_T, 128, 512), id, ks > 0 ? 1u : 0u);
       }
@@ -189,8 +193,10 @@ __global__ void __launch_bounds__(kThreads, 1) env4_fused_kernel(const Env4Fused
       tmem_ld32(tmem + lane_base + COL_S1 + h * 32, v);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        put16<2, X3>(sm + OFF_X + sw128_chunk_off(l2 * 16 + bl * 8 + h * 4 + i, l1), v + i * 8, SZ_X);
+        put16<2, X3>(sm + OFF_W + sw128_chunk_off(l2 * 16 + bl * 8 + h * 4 + i, l1), v + i * 8, SZ_W);
     }
+    // the E buffer was read only by S1, complete now
+    if (j + 1 < n_bt) store_e<X3>(sm, tid, nxt);
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
@@ -199,8 +205,8 @@ __global__ void __launch_bounds__(kThreads, 1) env4_fused_kernel(const Env4Fused
       tc_after_sync();
       const uint32_t id = idesc<2>(128, 64);
       for (int ks = 0; ks < 4; ++ks) {
-        const uint32_t ao = sbase + OFF_X + ks * 32, bo = sbase + OFF_A1 + ks * 256;
-        issue3<X3>(tmem + COL_S2, sdesc_sw128(ao), sdesc_sw128(ao + SZ_X), sdesc(bo, 128, 1024),
+        const uint32_t ao = sbase + OFF_W + ks * 32, bo = sbase + OFF_A1 + ks * 256;
+        issue3<X3>(tmem + COL_S2, sdesc_sw128(ao), sdesc_sw128(ao + SZ_W), sdesc(bo, 128, 1024),
                    sdesc(bo + SZ_A1, 128, 1024), id, ks > 0 ? 1u : 0u);
       }
       commit(&bar[1]);
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1) env4_fused_kernel(const Env4Fused
       tmem_ld32(tmem + lane_base + COL_S2 + h * 32, v);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        put16<2, X3>(sm + OFF_Y + kmajor_off(bl * 64 + (h * 4 + i) * 8 + al, l2 * 8, 8), v + i * 8, SZ_Y);
+        put16<2, X3>(sm + OFF_W + kmajor_off(bl * 64 + (h * 4 + i) * 8 + al, l2 * 8, 8), v + i * 8, SZ_W);
     }
     fence_async_smem();
     tc_before_sync();
@@ -223,8 +229,8 @@ __global__ void __launch_bounds__(kThreads, 1) env4_fused_kernel(const Env4Fused
       tc_after_sync();
       const uint32_t id = idesc<2>(128, 64);
       for (int ks = 0; ks < 4; ++ks) {
-        const uint32_t ao = sbase + OFF_Y + ks * 256, bo = sbase + OFF_A2 + ks * 256;
-        issue3<X3>(tmem + COL_S3, sdesc(ao, 128, 1024), sdesc(ao + SZ_Y, 128, 1024), sdesc(bo, 128, 1024),
+        const uint32_t ao = sbase + OFF_W + ks * 256, bo = sbase + OFF_A2 + ks * 256;
+        issue3<X3>(tmem + COL_S3, sdesc(ao, 128, 1024), sdesc(ao + SZ_W, 128, 1024), sdesc(bo, 128, 1024),
                    sdesc(bo + SZ_A2, 128, 1024), id, ks > 0 ? 1u : 0u);
       }
       commit(&bar[2]);
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(kThreads, 1) env4_fused_kernel(const Env4Fused
       tmem_ld32(tmem + lane_base + COL_S3 + h * 32, v);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        put16<2, X3>(sm + OFF_Z + kmajor_off(r1 * 64 + (h * 4 + i) * 8 + al, bl * 8, 2), v + i * 8, SZ_Z);
+        put16<2, X3>(sm + OFF_W + kmajor_off(r1 * 64 + (h * 4 + i) * 8 + al, bl * 8, 2), v + i * 8, SZ_W);
     }
     fence_async_smem();
     tc_before_sync();
@@ -248,15 +254,17 @@ __global__ void __launch_bounds__(kThreads, 1) env4_fused_kernel(const Env4Fused
       const uint32_t id = idesc<2>(128, 32);
       const uint32_t bo = sbase + OFF_B + buf * 2 * SZ_B;
       for (int qq = 0; qq < 4; ++qq) {
-        const uint32_t ao = sbase + OFF_Z + qq * 4096;
-        issue3<X3>(tmem + COL_S4 + qq * 32, sdesc(ao, 128, 256), sdesc(ao + SZ_Z, 128, 256), sdesc(bo, 128, 256),
+        const uint32_t ao = sbase + OFF_W + qq * 4096;
+        issue3<X3>(tmem + COL_S4 + qq * 32, sdesc(ao, 128, 256), sdesc(ao + SZ_W, 128, 256), sdesc(bo, 128, 256),
                    sdesc(bo + SZ_B, 128, 256), id, j > 0 ? 1u : 0u);
       }
       if (j + 1 == n_bt) commit(&bar[3]);
     }
-    // the other buffer was last read by the MMAs of tile j-1, complete since bar[0] of j
+    // the other B buffer was last read by S4 of tile j-1, complete since bar[0] of j; Z
+    // stays in the shared buffer until S4 completes, which the next S1 commit covers (one
+    // CTA's products run in issue order) before the next S1 epilogue overwrites it
     if (j + 1 < n_bt) {
-      store_slice<X3>(sm, buf ^ 1, tid, nxt);
+      store_b<X3>(sm, buf ^ 1, tid, nxt);
       fence_async_smem();
     }
     tc_before_sync();
