@@ -10,12 +10,22 @@ Dc=32, 512 chains (seeded iid N(0,1) tensors standing in for optimised PEPS).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun each rank runs its own chains (weak scaling, no data-path
-collective); rank 0 prints one JSON line.
+The JSON line carries the chosen form (split-BF16 tensor cores with the fused column
+steps, batched chains, graph-replayed steps) and, in ``arms``, plain FP32 batched and
+plain FP32 with one chain per launch, each with raw and effective samples/s (samples/s
+over 2 tau_int) and the energy difference against the chosen form on the same
+configurations.  Under torchrun every rank runs its own chains (weak scaling); the one
+collective is the all-reduce of the float64 gradient sums before the identical sign-SGD
+step of every rank.  Rank 0 prints one JSON line.
+
+Measurement helpers (not part of the timed line):
+    python bench.py --case env3|env4|step   one launch shape or one profiled step
+    python bench.py --study mixing|cutoff    plain vs learned sampler; convergence in Dc
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -32,8 +42,16 @@ UNIT = "samples/s"
 # FP32 CUDA-core peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
+# DRAM traffic of one bulk launch of the fused four-line step (Dc 32, D 8, 512 chains),
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the kernel whose
+# source hashed to `source_sha`; the bench reports it only while the source is unchanged.
+NCU_TRAFFIC = {
+    "fused4": {"bytes_per_launch": None, "chains": 512, "source": "paper_1908_09359_gb300/csrc/fused_env4.cu",
+               "source_sha": None, "summary": "profiles/fused4_env4_bulk_peps24x24.md"},
+}
 
-def parse():
+
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=2)
@@ -48,19 +66,49 @@ def parse():
                    help="measurement cutoff Dc2 (default 0: the same as the sampling cutoff)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    return p.parse_args()
+    p.add_argument("--no-arms", action="store_true", help="skip the plain-FP32 comparison arms")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle work per core for cpu_baseline")
+    # measurement helpers
+    p.add_argument("--case", choices=["env3", "env4", "step"], default=None)
+    p.add_argument("--chains", type=int, default=None)
+    p.add_argument("--reps", type=int, default=10)
+    p.add_argument("--separate", action="store_true", help="--case env3/env4: three/four separate products")
+    p.add_argument("--top", type=int, default=25)
+    p.add_argument("--study", choices=["mixing", "cutoff"], default=None)
+    p.add_argument("--structured", action="store_true", help="bond spectra exp(-i) instead of iid tensors")
+    p.add_argument("--therm", type=int, default=50)
+    p.add_argument("--sweeps", type=int, default=200)
+    p.add_argument("--collect", type=int, default=100)
+    p.add_argument("--epochs", type=int, default=20)
+    p.add_argument("--lr", type=float, default=2e-3)
+    p.add_argument("--arms", default="plain,learned")
+    p.add_argument("--L", type=int, default=16)
+    p.add_argument("--D", type=int, default=4)
+    p.add_argument("--cutoffs", default="4,8,12,16,24,32")
+    p.add_argument("--ref", type=int, default=64)
+    p.add_argument("--cutoff-sweeps", type=int, default=10)
+    return p.parse_args(argv)
 
+
+# ------------------------------------------------------------------ multi-rank helpers
 
 def dist_info():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
-def rank_seeds(w, rank):
-    """One rank's share of the workload: the tensors are replicated, every rank runs its
-    own n_chains chains with its own start configurations and Metropolis key (weak
-    scaling over independent Markov chains; no data-path collective)."""
-    return {"spins": w["seed"] + 7919 * rank, "key": w["seed"] + rank}
+def rank_share(w, rank, world):
+    """One rank's share of a job of world x n_chains chains: its start configurations
+    (a slice of the job's seeded starts) and the global index of its first chain (the
+    chain word of the Philox counters), with the job's one key on every rank so that
+    the sign-SGD draws -- and therefore the updated tensors -- are identical."""
+    import numpy as np
+
+    from paper_1908_09359_gb300 import inputs
+    C = w["n_chains"]
+    starts = inputs.start_spins(world * C, w["Ly"], w["Lx"], w["seed"], "random")
+    return {"spins": np.ascontiguousarray(starts[rank * C:(rank + 1) * C]), "chain_offset": rank * C,
+            "key": w["seed"]}
 
 
 def max_over_ranks(x, dist, device):
@@ -132,6 +180,18 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(path)) if os.path.exists(path) else {}
+    bf16 = (peaks.get("bf16_tflops_sustained"), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)")
+    if bf16[0] is None:
+        bf16 = (1700.0, "fallback sustained bf16 1.7 PFLOP/s (of fallback)")
+    hbm = (peaks.get("hbm_gbs"), "MEASURED_PEAKS.json hbm_gbs (of measured)")
+    if hbm[0] is None:
+        hbm = (6800.0, "fallback 6.8 TB/s (of fallback)")
+    return bf16, hbm
+
+
 def binding_roofline(flops, nbytes, seconds, compute_peak, hbm_peak):
     """(binding roof, other roof, flop per byte, ridge) of a kernel that did `flops`
     algorithmic flops over `nbytes` algorithmic bytes in `seconds`.  compute_peak =
@@ -153,11 +213,34 @@ def binding_roofline(flops, nbytes, seconds, compute_peak, hbm_peak):
     return compute, memory, intensity, ridge
 
 
-def oracle_sample_seconds(name, reps=1):
-    """Seconds per sample of the FP64 oracle on this host, from a bounded sample of the
-    workload: one bulk-row truncation fit, one sampling row, one measurement row (three-
-    line) and one row pair (four-line), each timed once on one chain and weighted by how
-    often a step performs it.  Returns (seconds, description, threads)."""
+def kernel_groups(shapes):
+    """Per-launch-shape profile records -> totals per kernel: the fused four-line and
+    three-line steps, the separate tensor-core and FP32 products, the QR."""
+    groups = {}
+    for r in shapes:
+        s = r["shape"]
+        g = ("fused4" if s.startswith("fused4") else "fused3" if s.startswith("fused3") else
+             "gemm_tc" if s.startswith("gemm tc") else "gemm_f32" if s.startswith("gemm f32") else
+             "qr" if s.startswith("qr") else "other")
+        acc = groups.setdefault(g, {"launches": 0, "flops": 0.0, "ms": 0.0})
+        acc["launches"] += r["launches"]
+        acc["flops"] += r["flops"]
+        acc["ms"] += r["ms"]
+    return groups
+
+
+def source_sha(rel):
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ the oracle on the host
+
+def oracle_bounded_sample(name, chain):
+    """Seconds of FP64 oracle work for a bounded sample of one chain's sample step, and
+    the fraction of a full sample that work stands for: one bulk-row truncation fit, one
+    sampling row, one measurement row (three-line) and one row pair (four-line), each
+    weighted by how often a step performs it."""
     import numpy as np
 
     from oracle import vmc
@@ -165,35 +248,72 @@ def oracle_sample_seconds(name, reps=1):
     w = inputs.workload(name, n_chains=1)
     Ly, Lx, chi = w["Ly"], w["Lx"], w["chi"]
     g = vmc.unpack(w["tensors"], Ly, Lx, w["D"])
-    sp = np.array(w["spins"][0])
+    sp = np.array(inputs.start_spins(chain + 1, Ly, Lx, w["seed"], "random")[chain])
     k = min(3, Ly - 2)
     Ts, _ = vmc.top_envs(g, sp, chi, w["sketch"], 3, upto=k + 1)
     Bs = Ts  # any bond-saturated MPS of the right shape stands in for the bottom environment
-    best = None
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        vmc.compress(vmc.mpo_times_mps(Ts[k], vmc.row_tensors(g, sp, k)), chi, w["sketch"], 3)
-        t1 = time.perf_counter()
-        vmc._sample_row(g, sp.copy(), k, Ts[k], Bs[k + 1], 1, 0, 0, 0, None)
-        t2 = time.perf_counter()
-        G = [[None] * Lx for _ in range(Ly)]
-        vmc._row_terms(g, sp, k, Ts[k], Bs[k + 1], w["J1"], G, [0.0])
-        t3 = time.perf_counter()
-        vmc._pair_terms(g, sp, k, Ts[k], Bs[k + 1], w["J1"], w["J2"], [0.0])
-        t4 = time.perf_counter()
-        cur = (t1 - t0, t2 - t1, t3 - t2, t4 - t3)
-        best = cur if best is None or sum(cur) < sum(best) else best
-    n_fit = 2 * (Lx - 1) + 2 * (Ly - 1) + (Ly - 1)   # two sweep phases x two directions + fresh bottom
-    per_sample = n_fit * best[0] + (Lx + Ly) * best[1] + Ly * best[2] + (Ly - 1) * best[3]
-    desc = (f"{name}, 1 chain: one bulk-row fit ({best[0]:.2f}s) x{n_fit}, one sampling row "
-            f"({best[1]:.2f}s) x{Lx + Ly}, one three-line measurement row ({best[2]:.2f}s) x{Ly}, one "
-            f"four-line row pair ({best[3]:.2f}s) x{Ly - 1}; summed = s/sample")
-    try:
-        from threadpoolctl import threadpool_info
-        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
-    except Exception:
-        threads = os.cpu_count()
-    return per_sample, desc, threads, sum(best)
+    t0 = time.perf_counter()
+    vmc.compress(vmc.mpo_times_mps(Ts[k], vmc.row_tensors(g, sp, k)), chi, w["sketch"], 3)
+    t1 = time.perf_counter()
+    vmc._sample_row(g, sp.copy(), k, Ts[k], Bs[k + 1], 1, chain, 0, 0, None)
+    t2 = time.perf_counter()
+    G = [[None] * Lx for _ in range(Ly)]
+    vmc._row_terms(g, sp, k, Ts[k], Bs[k + 1], w["J1"], G, [0.0])
+    t3 = time.perf_counter()
+    vmc._pair_terms(g, sp, k, Ts[k], Bs[k + 1], w["J1"], w["J2"], [0.0])
+    t4 = time.perf_counter()
+    parts = (t1 - t0, t2 - t1, t3 - t2, t4 - t3)
+    counts = (2 * (Lx - 1) + 2 * (Ly - 1) + (Ly - 1), Lx + Ly, Ly, Ly - 1)
+    per_sample = sum(c * p for c, p in zip(counts, parts))
+    return sum(parts), sum(parts) / per_sample, parts, counts
+
+
+def _oracle_worker(job):
+    name, chain, seconds = job
+    work = frac = 0.0
+    parts = counts = None
+    while work < seconds:
+        s, f, parts, counts = oracle_bounded_sample(name, chain)
+        work += s
+        frac += f
+    return work, frac, parts, counts
+
+
+def _one_thread():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        os.environ[v] = "1"
+
+
+def oracle_rate(name, procs, seconds):
+    """Samples/s of the FP64 oracle with `procs` single-threaded processes (spawned),
+    each running bounded samples of its own chain for about `seconds` of work; the
+    chains are independent, so all cores work in parallel.  Returns a dict with
+    value, cores, wall seconds and a description of the sample."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(procs, initializer=_one_thread) as pool:
+        res = pool.map(_oracle_worker, [(name, c, seconds) for c in range(procs)])
+    wall = time.perf_counter() - t0
+    samples = sum(r[1] for r in res)
+    parts, counts = res[0][2], res[0][3]
+    desc = (f"{name}: {procs} single-threaded processes, one chain each, ~{seconds:.0f} s of work each, "
+            "repeating one bounded sample = one bulk-row fit ({:.2f}s) x{}, one sampling row ({:.2f}s) x{}, "
+            "one three-line measurement row ({:.2f}s) x{}, one four-line row pair ({:.2f}s) x{} of a full "
+            "sample; samples counted as the fraction of a full sample done; rate = samples / wall "
+            "(extrapolated from the bounded sample)").format(parts[0], counts[0], parts[1], counts[1], parts[2],
+                                                              counts[2], parts[3], counts[3])
+    return {"value": samples / wall, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": desc,
+            "wall_s": wall, "samples_equivalent": samples}
+
+
+def cpu_baselines(name, seconds):
+    one = oracle_rate(name, 1, seconds)
+    cores = os.cpu_count() or 1
+    allc = oracle_rate(name, cores, seconds) if cores > 1 else one
+    out = dict(allc)
+    out["one_core"] = {"value": one["value"], "cores": 1, "wall_s": one["wall_s"]}
+    return out
 
 
 def run_reference(args):
@@ -202,34 +322,151 @@ def run_reference(args):
         return
     from paper_1908_09359_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
+    cores = os.cpu_count() or 1
+    per_step = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_sample_seconds(args.workload)
-    per = []
-    cpu = None
+        oracle_rate(args.workload, cores, per_step / 4)
+    walls, samples, last = [], 0.0, None
     for _ in range(args.steps):
-        s, desc, threads, work = oracle_sample_seconds(args.workload)
-        per.append(s)
-        cpu = (desc, threads, work)
-    sec = statistics.median(per)
-    value = 1.0 / sec
+        last = oracle_rate(args.workload, cores, per_step)
+        walls.append(last["wall_s"])
+        samples += last["samples_equivalent"]
+    wall = sum(walls)
+    value = samples / wall
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded iid N(0,1) PEPS tensors)",
         "config": {"workload": args.workload, "Ly": w["Ly"], "Lx": w["Lx"], "D": w["D"], "Dc": w["chi"],
-                   "J2": w["J2"], "chains": 1, "n_fit": 3},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu[1], "kind": "oracle", "sample": cpu[0]},
+                   "J2": w["J2"], "n_fit": 3,
+                   "step": "a bounded sample of every core's chain (timed wall seconds per step in ms_per_step; "
+                           "samples counted as the fraction of a full sample done)"},
+        "timed_seconds": wall, "samples_equivalent": samples,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": last["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
+# ------------------------------------------------------------------ our arm
+
+def make_ctx(w, n_chains, precision, share=None, chi=None, chi_measure=0, n_fit=3, tensors=None):
+    from paper_1908_09359_gb300 import api, inputs
+    chi_s = chi or w["chi"]
+    chi_x = max(chi_s, chi_measure)
+    sk = w["sketch"] if chi_x == w["chi"] else inputs.sketch(max(w["Ly"], w["Lx"]), chi_x, w["D"], w["seed"])
+    share = share or {"key": w["seed"], "chain_offset": 0}
+    ctx = api.PepsVMC(w["Ly"], w["Lx"], w["D"], chi_s, n_chains, w["tensors"] if tensors is None else tensors, sk,
+                      J1=w["J1"], J2=w["J2"], seed=share["key"], n_fit=n_fit, precision=api.PRECISIONS[precision],
+                      chi_measure=chi_measure, chain_offset=share["chain_offset"])
+    return ctx
+
+
+def timed_steps(ctx, steps, warmup, delta=1e-3, dist=None, collect=True, step0=0):
+    """warmup + steps hot-path steps (energy_and_grad(1), the gradient-sum all-reduce
+    when several ranks run, sign-SGD); CUDA events bracket the timed steps.  Returns
+    (ms, eloc (steps, C), mz2 (steps, C), launches)."""
     import numpy as np
     import torch
 
-    from paper_1908_09359_gb300 import api, inputs
+    from paper_1908_09359_gb300 import autocorr, dist as xdist
+
+    def step(i):
+        r = ctx.energy_and_grad(1, want_samples=collect, want_grad=False)
+        if dist:
+            xdist.allreduce_device(ctx)
+        ctx.update(delta, step0 + i)
+        return r
+
+    for i in range(warmup):
+        step(i)
+    stream = torch.cuda.current_stream()
+    el, mz = [], []
+    l0 = ctx.launches
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        r = step(warmup + i)
+        if collect:
+            el.append(r["eloc"])
+            mz.append(autocorr.staggered_mz2(ctx.get_spins()))
+    e1.record(stream)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), np.array(el), np.array(mz), ctx.launches - l0
+
+
+def tau_of(el, mz):
+    from paper_1908_09359_gb300 import autocorr
+    if len(el) < 2:
+        return None, None
+    return autocorr.tau_int(el)[0], autocorr.tau_int(mz)[0]
+
+
+def precision_gap(ctx_a, ctx_b, spins, N):
+    """E_loc of the same configurations in two contexts: |dE_loc| / N, mean and max."""
+    import numpy as np
+    ctx_a.set_spins(spins)
+    ctx_b.set_spins(spins)
+    ea, _, _ = ctx_a.measure()
+    eb, _, _ = ctx_b.measure()
+    d = np.abs(ea - eb) / N
+    return {"mean_abs_dE_per_site": float(d.mean()), "max_abs_dE_per_site": float(d.max()),
+            "configs": int(len(d))}
+
+
+def run_arms(args, w, chosen, spins_final, tau, C):
+    """Plain FP32 batched, plain FP32 one chain per launch, and the precision gap of the
+    chosen form on identical configurations (iid and bond-decay tensors)."""
+    import numpy as np
+
+    from paper_1908_09359_gb300 import inputs
+    N = w["Ly"] * w["Lx"]
+    arms = {}
+    fp = make_ctx(w, C, "fp32", chi=args.chi, chi_measure=args.chi_measure, n_fit=args.n_fit)
+    fp.set_spins(rank_share(w, 0, 1)["spins"])
+    ms, _, _, _ = timed_steps(fp, 1, 2, collect=False)
+    sps = C / (ms / 1e3)
+    arms["plain_fp32_batched"] = {"samples_per_s": sps, "eff_samples_per_s": sps / (2 * tau) if tau else None,
+                                  "chains_per_launch": C, "steps": 1, "warmup": 2, "ms_per_step": ms,
+                                  "tau_int": tau, "tau_note": "the chosen form's tau_int (same transition rule)"}
+    arms["precision_gap_iid"] = precision_gap(chosen, fp, spins_final, N)
+    fp.close()
+    one = make_ctx(w, 1, "fp32", chi=args.chi, chi_measure=args.chi_measure, n_fit=args.n_fit)
+    one.set_spins(rank_share(w, 0, 1)["spins"][:1])
+    ms, _, _, launches = timed_steps(one, 2, 2, collect=False)
+    sps = 2 / (ms / 1e3)
+    arms["plain_fp32_single_chain"] = {"samples_per_s": sps,
+                                       "eff_samples_per_s": sps / (2 * tau) if tau else None,
+                                       "chains_per_launch": 1, "steps": 2, "warmup": 2, "ms_per_step": ms / 2,
+                                       "launches_per_step": launches / 2, "tau_int": tau}
+    one.close()
+    # bond spectra exp(-i) (App. A's simple-update form): the contraction is well
+    # conditioned there, so the gap measures the precision, not chaos of the truncation
+    sd = inputs.peps_tensors(w["Ly"], w["Lx"], w["D"], w["seed"], w["normalise"], bond_decay=1.0)
+    nb = min(C, 64)
+    a = make_ctx(w, nb, args.precision, chi=args.chi, chi_measure=args.chi_measure, n_fit=args.n_fit, tensors=sd)
+    b = make_ctx(w, nb, "fp32", chi=args.chi, chi_measure=args.chi_measure, n_fit=args.n_fit, tensors=sd)
+    a.set_spins(rank_share(w, 0, 1)["spins"][:nb])
+    a.sample_sweep(2)
+    arms["precision_gap_bond_decay"] = precision_gap(a, b, a.get_spins(), N)
+    a.close()
+    b.close()
+    return arms
+
+
+def run_ours(args):
+    import ctypes as ct
+
+    import numpy as np
+    import torch
+
+    from paper_1908_09359_gb300 import inputs
     rank, world, local = dist_info()
     dist = None
     if world > 1:
@@ -238,146 +475,157 @@ def run_ours(args):
     torch.cuda.set_device(local)
     w = inputs.workload(args.workload)
     C = w["n_chains"]
-    seeds = rank_seeds(w, rank)
-    spins = inputs.start_spins(C, w["Ly"], w["Lx"], seeds["spins"], "random")
-    prec = api.PRECISIONS[args.precision]
-    chi_s = args.chi or w["chi"]
-    chi_x = max(chi_s, args.chi_measure)
-    sk = w["sketch"] if chi_x == w["chi"] else inputs.sketch(max(w["Ly"], w["Lx"]), chi_x, w["D"], w["seed"])
-    ctx = api.PepsVMC(w["Ly"], w["Lx"], w["D"], chi_s, C, w["tensors"], sk, J1=w["J1"],
-                      J2=w["J2"], seed=seeds["key"], n_fit=args.n_fit, precision=prec, chi_measure=args.chi_measure)
-    ctx.set_spins(spins)
-    delta = 1e-3
+    N = w["Ly"] * w["Lx"]
+    share = rank_share(w, rank, world)
+    ctx = make_ctx(w, C, args.precision, share, args.chi, args.chi_measure, args.n_fit)
+    ctx.set_spins(share["spins"])
 
-    def step(i, host=None):
-        if host is None:
-            ctx.energy_and_grad(1, want_samples=False, want_grad=False)
-        else:
-            ctx.set_tensors(host["tensors"])
-            ctx._check(ctx.lib.pepsvmc_energy_and_grad(ctx.ctx, 1, None, None, host["p_eloc"],
-                                                       host["p_logpsi"], host["p_sign"], host["p_grad"]))
-        ctx.update(delta, i)
-        if host is not None:
-            ctx._check(ctx.lib.pepsvmc_get_tensors(ctx.ctx, host["p_tensors"]))
-
-    def barrier():
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    for i in range(args.warmup):
-        step(i)
-    stream = torch.cuda.current_stream()
-    l0 = ctx.launches
-    barrier()
     with Clocks(local) as clk:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for i in range(args.steps):
-            step(args.warmup + i)
-        e1.record(stream)
-        barrier()
-    launches = ctx.launches - l0
-    ms = e0.elapsed_time(e1)
-    # Roofline of the contraction kernel: one more step with every contraction launch
-    # bracketed by CUDA events on the library's stream (eager, so the events can sit
-    # between launches; the timed steps above replay a CUDA graph without them).
+        ms, el, mz, launches = timed_steps(ctx, args.steps, args.warmup, dist=dist)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_rate(world, C, args.steps, ms / 1e3)
+    tau_e, tau_m = tau_of(el, mz)
+    tau = max(tau_e, tau_m) if tau_e is not None else None
+    spins_final = ctx.get_spins()
+
+    # one further step with per-launch CUDA events on the library's stream (eager, so
+    # the events sit between launches; the timed steps replay a CUDA graph)
+    stream = torch.cuda.current_stream()
     ctx.set_profiling(True)
     pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     pe0.record(stream)
-    step(args.warmup + args.steps)
+    ctx.energy_and_grad(1, want_samples=False, want_grad=False)
+    ctx.update(1e-3, 10 ** 6)
     pe1.record(stream)
     torch.cuda.synchronize()
     prof = ctx.get_profile()
+    shapes = ctx.get_profile_shapes()
     prof_step_ms = pe0.elapsed_time(pe1)
     ctx.set_profiling(False)
-    ms = max_over_ranks(ms, dist, "cuda")
-    value = whole_job_rate(world, C, args.steps, ms / 1e3)
 
     e2e = None
     if not args.no_e2e:
-        import ctypes as ct
+        # through the C ABI with host buffers: the tensors uploaded from pinned memory,
+        # E_loc / ln|Psi| / sign and the gradient read back, the updated tensors read back
         P = ctx.n_params
         pin = lambda n, dt: torch.empty(n, dtype=dt).pin_memory().numpy()  # noqa: E731
         host = dict(tensors=pin(P, torch.float64), eloc=pin(C, torch.float64), logpsi=pin(C, torch.float64),
                     sign=pin(C, torch.int8), grad=pin(P, torch.float64), out=pin(P, torch.float64))
         host["tensors"][:] = ctx.get_tensors()
         dp = lambda a: a.ctypes.data_as(ct.POINTER(ct.c_double))  # noqa: E731
-        host.update(p_eloc=dp(host["eloc"]), p_logpsi=dp(host["logpsi"]),
-                    p_sign=host["sign"].ctypes.data_as(ct.POINTER(ct.c_int8)), p_grad=dp(host["grad"]),
-                    p_tensors=dp(host["out"]))
-        barrier()
+        from paper_1908_09359_gb300 import dist as xdist
+        n_e2e = max(1, min(args.steps, 3))
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i in range(args.steps):
-            step(args.warmup + args.steps + 1 + i, host)
-        barrier()
+        for i in range(n_e2e):
+            ctx.set_tensors(host["tensors"])
+            ctx._check(ctx.lib.pepsvmc_energy_and_grad(ctx.ctx, 1, None, None, dp(host["eloc"]), dp(host["logpsi"]),
+                                                       host["sign"].ctypes.data_as(ct.POINTER(ct.c_int8)),
+                                                       dp(host["grad"])))
+            if dist:
+                xdist.allreduce_device(ctx)
+            ctx.update(1e-3, 2 * 10 ** 6 + i)
+            ctx._check(ctx.lib.pepsvmc_get_tensors(ctx.ctx, dp(host["out"])))
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        e2e = {"value": whole_job_rate(world, C, args.steps, max_over_ranks(e2e_s, dist, "cuda")), "unit": UNIT,
-               "h2d_bytes_per_step": P * 8,
-               "d2h_bytes_per_step": C * (8 + 8 + 1) + 2 * P * 8}
+        e2e = {"value": whole_job_rate(world, C, n_e2e, max_over_ranks(e2e_s, dist, "cuda")), "unit": UNIT,
+               "h2d_bytes_per_step": P * 8, "d2h_bytes_per_step": C * (8 + 8 + 1) + 2 * P * 8, "steps": n_e2e}
 
     if rank != 0:
+        ctx.close()
         if dist:
             dist.destroy_process_group()
         return
-    step_ms = ms / args.steps
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    hbm, hbm_src = peaks.get("hbm_gbs"), "MEASURED_PEAKS.json hbm_gbs (of measured)"
-    if hbm is None:
-        hbm, hbm_src = 6800.0, "fallback 6.8 TB/s (of fallback)"
-    if args.precision == "fp32":
-        kname = "gemm_f32_kernel (batched contraction, FP32 CUDA cores)"
-        cbound, cpeak = "alu", FP32_ALU_PEAK_TFLOPS
-        csrc = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"
-    else:
-        bf16 = peaks.get("bf16_tflops_sustained")
-        src = "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
-        if bf16 is None:
-            bf16, src = 1700.0, "fallback sustained bf16 1.7 PFLOP/s (of fallback)"
-        # TF32 dense rate is half the BF16 rate; split BF16 issues three BF16 MMAs per
-        # product, so its algorithmic flops are reported against a third of the BF16 peak
-        cpeak = {"bf16": bf16, "tf32": bf16 / 2.0, "bf16x3": bf16 / 3.0}[args.precision]
-        kname = ("gemm_tc_kernel (batched contraction, tcgen05 "
-                 + {"bf16": "kind::f16", "tf32": "kind::tf32", "bf16x3": "kind::f16, split hi+lo, 3 MMAs"}[
-                     args.precision] + ", tile autotuned per shape)")
-        cbound = "tensor"
-        csrc = src + {"bf16": "", "tf32": " x 1/2 for TF32", "bf16x3": " x 1/3 for three BF16 MMAs"}[args.precision]
-    bind, other, intensity, ridge = binding_roofline(prof["gemm_flops"], prof["gemm_bytes"], prof["gemm_ms"] / 1e3,
-                                                     (cbound, cpeak, csrc), (hbm, hbm_src))
-    flops, nbytes = prof["gemm_flops"], prof["gemm_bytes"]
-    roofline = {
-        "kernel": kname, "bound": bind["bound"], "achieved": bind["achieved"], "peak": bind["peak"],
-        "unit": bind["unit"], "frac": bind["frac"], "peak_source": bind["peak_source"],
-        "traffic": None,
-        "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
-        "other_roof": other,
-        "algorithmic_flops_per_step": flops, "algorithmic_bytes_per_step": nbytes,
-        "share_of_step": prof["gemm_ms"] / prof_step_ms,
-        "launches": prof["gemm_launches"],
-        "qr_ms_per_step": prof["qr_ms"],
-        "measured_on": "one extra eager step with per-launch CUDA events on the library's stream (ms %.0f)"
-                       % prof_step_ms,
-    }
+
+    (bf16, bf16_src), (hbm, hbm_src) = measured_peaks()
+    groups = kernel_groups(shapes)
+    contraction = {k: v for k, v in groups.items() if k != "qr" and k != "other"}
+    dominant = max(contraction, key=lambda k: contraction[k]["ms"]) if contraction else None
+    roofline = None
+    if dominant:
+        bulk = None
+        if dominant in ("fused4", "fused3"):
+            key = "fused4 32 32 32 32" if dominant == "fused4" else "fused3 32 32 32 32 x 8 8 8 8"
+            bulk = next((r for r in shapes if r["shape"] == key), None)
+        rec = bulk or {"shape": dominant, **contraction[dominant]}
+        per_launch_flops = rec["flops"] / rec["launches"]
+        per_launch_ms = rec["ms"] / rec["launches"]
+        if args.precision == "fp32":
+            cpeak, csrc, cbound = FP32_ALU_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)", "alu"
+        else:
+            cpeak, csrc, cbound = bf16, bf16_src + "; algorithmic flops counted once (split BF16 issues three " \
+                                                    "BF16 MMAs per product)", "tensor"
+        # algorithmic bytes of one bulk fused launch: E, T, B and the result per chain in FP32
+        chi, D = w["chi"], w["D"]
+        nbytes = None
+        if rec["shape"].startswith("fused4"):
+            nbytes = 4.0 * C * (chi * D * D * chi * 2 + 2 * chi * D * chi)
+        elif rec["shape"].startswith("fused3"):
+            nbytes = 4.0 * C * 4 * chi * D * chi
+        achieved = per_launch_flops / (per_launch_ms / 1e3) / 1e12
+        traffic = None
+        t = NCU_TRAFFIC.get(dominant)
+        if t and rec is bulk and t["bytes_per_launch"] and t["source_sha"] == source_sha(t["source"]):
+            traffic = t["bytes_per_launch"] * C / t["chains"]
+        step_flops = prof["gemm_flops"]
+        roofline = {
+            "kernel": {"fused4": "env4_fused_kernel (four-line column step, tcgen05, split BF16)",
+                       "fused3": "env3_fused_kernel (three-line column step, tcgen05, split BF16)",
+                       "gemm_tc": "gemm_tc_kernel (separate products, tcgen05)",
+                       "gemm_f32": "gemm_f32_kernel (separate products, FP32 CUDA cores)"}[dominant],
+            "shape": rec["shape"], "bound": cbound, "achieved": achieved, "peak": cpeak, "unit": "TFLOP/s",
+            "frac": achieved / cpeak, "peak_source": csrc, "traffic": traffic,
+            "traffic_source": (t["summary"] if traffic else "null: no ncu capture of this kernel source"),
+            "flops_per_launch": per_launch_flops, "ms_per_launch": per_launch_ms,
+            "algorithmic_bytes_per_launch": nbytes,
+            "intensity_flop_per_byte": per_launch_flops / nbytes if nbytes else None,
+            "ridge_flop_per_byte": cpeak * 1e12 / (hbm * 1e9), "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src,
+            "launches_of_shape_per_step": rec["launches"],
+            "step_contraction": {
+                "algorithmic_flops": step_flops, "ms": prof["gemm_ms"],
+                "tflops": step_flops / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else None,
+                "frac_of_peak": (step_flops / (prof["gemm_ms"] / 1e3) / 1e12) / cpeak if prof["gemm_ms"] > 0 else None,
+                "method_frac": (step_flops / (prof_step_ms / 1e3) / 1e12) / cpeak,
+                "method_frac_note": "all contraction flops of the step over the whole step's time",
+                "share_of_step": prof["gemm_ms"] / prof_step_ms, "qr_ms": prof["qr_ms"],
+                "profiled_step_ms": prof_step_ms,
+                "shares": {k: v["ms"] / prof_step_ms for k, v in groups.items()},
+            },
+        }
+    arms = None
+    if not args.no_arms and world == 1:
+        arms = run_arms(args, w, ctx, spins_final, tau, C)
+        eff = value / (2 * tau) if tau else None
+        if eff and arms["plain_fp32_single_chain"]["eff_samples_per_s"]:
+            arms["chosen_over_single_chain_fp32_eff"] = eff / arms["plain_fp32_single_chain"]["eff_samples_per_s"]
+            arms["chosen_over_batched_fp32_eff"] = eff / arms["plain_fp32_batched"]["eff_samples_per_s"]
+    ctx.close()
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        s, desc, threads, _ = oracle_sample_seconds(args.workload)
-        cpu = {"value": 1.0 / s, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        cpu = cpu_baselines(args.workload, args.cpu_seconds)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 operands, f32 accumulate",
                                       "tf32": "tf32 operands, f32 accumulate",
                                       "bf16x3": "bf16 hi+lo operands, f32 accumulate"}[args.precision],
         "data": "synthetic (seeded iid N(0,1) PEPS tensors, random S^z=0 starts)",
-        "config": {"workload": args.workload, "Ly": w["Ly"], "Lx": w["Lx"], "D": w["D"], "Dc": chi_s,
-                   "Dc_measure": args.chi_measure or chi_s,
+        "config": {"workload": args.workload, "Ly": w["Ly"], "Lx": w["Lx"], "D": w["D"], "Dc": args.chi or w["chi"],
+                   "Dc_measure": args.chi_measure or args.chi or w["chi"],
                    "J1": w["J1"], "J2": w["J2"], "chains_per_gpu": C, "n_fit": args.n_fit,
                    "form": {"fp32": "plain FP32", "bf16": "mixed BF16 (tcgen05)", "tf32": "mixed TF32 (tcgen05)",
-                            "bf16x3": "mixed split-BF16 (tcgen05)"}[args.precision], "step": "sweep + measure + gradient sums + sign-SGD",
+                            "bf16x3": "mixed split-BF16 (tcgen05, fused column steps)"}[args.precision],
+                   "step": "sweep + measure + gradient sums (+ all-reduce when N > 1) + sign-SGD",
                    "l2": "working set (boundary-MPS caches, GBs) larger than L2; no flush"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "tau_int": {"eloc": tau_e, "mz2": tau_m, "samples": int(el.size) if len(el) else 0,
+                    "estimator": "Sokal automatic window (c = 5) on the chain-averaged autocovariance of the "
+                                 "timed steps"},
+        "eff_samples_per_s": value / (2 * tau) if tau else None,
+        "roofline": roofline, "arms": arms, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -385,9 +633,201 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
+# ------------------------------------------------------------------ measurement helpers
+
+def run_case(args):
+    """--case env3 / env4: one bulk launch shape of the three- or four-line step through
+    the C ABI (the small, bounded cases that ncu captures use); --case step: one profiled
+    hot-path step with the per-shape device-time table."""
+    import torch
+
+    from paper_1908_09359_gb300 import api, inputs
+    w = inputs.workload(args.workload, n_chains=1)
+    n = args.chains or inputs.WORKLOADS[args.workload]["n_chains"]
+    D, chi = w["D"], w["chi"]
+    prec = api.PRECISIONS[args.precision]
+    if args.case == "step":
+        wl = inputs.workload(args.workload, n_chains=n)
+        ctx = api.PepsVMC(wl["Ly"], wl["Lx"], D, chi, n, wl["tensors"], wl["sketch"], J1=wl["J1"], J2=wl["J2"],
+                          seed=1, precision=prec)
+        ctx.set_spins(wl["spins"])
+        ctx.set_fused(not args.separate)
+        ctx.energy_and_grad(1, want_samples=False, want_grad=False)
+        ctx.set_profiling(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.energy_and_grad(1, want_samples=False, want_grad=False)
+        ctx.update(1e-3, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        rows = sorted(ctx.get_profile_shapes(), key=lambda r: -r["ms"])
+        total = sum(r["ms"] for r in rows)
+        print(json.dumps({"case": "step", "workload": args.workload, "precision": args.precision, "chains": n,
+                          "step_ms": e0.elapsed_time(e1), "profiled_ms": total}))
+        for r in rows[:args.top]:
+            tf = r["flops"] / (r["ms"] / 1e3) / 1e12 if r["ms"] > 0 else 0.0
+            print(f'{r["shape"]:32s} launches {r["launches"]:7d}  ms {r["ms"]:10.1f}  '
+                  f'share {r["ms"] / total:6.3f}  TFLOP/s {tf:7.2f}')
+        ctx.close()
+        return
+    ctx = api.PepsVMC(w["Ly"], w["Lx"], D, chi, n, w["tensors"], w["sketch"], seed=1, precision=prec)
+    ctx.set_fused(not args.separate)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    r = lambda *s: torch.randn(*s, generator=g, device="cuda")  # noqa: E731
+    spins = torch.where(torch.rand(n, generator=g, device="cuda") < 0.5, 1, -1).to(torch.int8)
+    if args.case == "env3":
+        E, T, B, A = r(n, chi, D, chi), r(n, chi, D, chi), r(n, chi, D, chi), r(2, D, D, D, D)
+        out = torch.empty(n, chi, D, chi, device="cuda")
+        dims = (n, chi, chi, chi, chi, D, D, D, D)
+        run = lambda: ctx.env3_left(E, T, A, spins, B, out, dims)  # noqa: E731
+        flops = 2.0 * (2 * chi ** 3 * D ** 2 + chi ** 2 * D ** 4) * n
+    else:
+        E, T, B = r(n, chi, D, D, chi), r(n, chi, D, chi), r(n, chi, D, chi)
+        A1, A2 = r(2, D, D, D, D), r(2, D, D, D, D)
+        out = torch.empty(n, chi, D, D, chi, device="cuda")
+        dims = (n, chi, chi, chi, chi, D, D, D, D, D, D, D)
+        run = lambda: ctx.env4_left(E, T, A1, spins, A2, spins, B, out, dims)  # noqa: E731
+        flops = 2.0 * (2 * chi ** 3 * D ** 3 + 2 * chi ** 2 * D ** 5) * n
+    for _ in range(3):
+        run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.reps
+    print(json.dumps({"case": args.case, "workload": args.workload, "precision": args.precision, "chains": n,
+                      "fused": not args.separate, "ms_per_launch": ms, "tflops": flops / (ms / 1e3) / 1e12}))
+    ctx.close()
+
+
+def _mixing_arm(ctx, start, sweep0, sweeps, N):
+    import numpy as np
+
+    from paper_1908_09359_gb300 import autocorr
+    ctx.set_spins(start)
+    ctx.set_sweep_counter(sweep0)
+    el = np.empty((sweeps, ctx.n_chains))
+    mz = np.empty((sweeps, ctx.n_chains))
+    secs = 0.0
+    for t in range(sweeps):
+        t0 = time.perf_counter()
+        r = ctx.energy_and_grad(1, want_samples=True, want_grad=True)
+        secs += time.perf_counter() - t0
+        el[t] = r["eloc"]
+        mz[t] = autocorr.staggered_mz2(ctx.get_spins())
+    e_mean, e_err = autocorr.mean_and_error(el / N)
+    tau_e, _ = autocorr.tau_int(el)
+    tau_m, _ = autocorr.tau_int(mz)
+    sps = sweeps * ctx.n_chains / secs
+    tau = max(tau_e, tau_m)
+    return dict(E_per_site=e_mean, E_err=e_err, tau_eloc=tau_e, tau_mz2=tau_m, Mz2=float(mz.mean()),
+                s_per_step=secs / sweeps, samples_per_s=sps, eff_samples_per_s=sps / (2 * tau))
+
+
+def study_mixing(args):
+    """Plain sequential sampler against plain + learned band moves from the same
+    thermalised configurations, one sample per chain per step through
+    pepsvmc_energy_and_grad: E per site with its tau-corrected error, tau_int of E_loc
+    and of M_z^2, raw and effective samples/s.  The network is trained first on the
+    plain sampler's configurations (one-off cost reported separately)."""
+    import numpy as np
+
+    from paper_1908_09359_gb300 import api, inputs
+    arms = args.arms.split(",")
+    w = inputs.workload(args.workload, n_chains=args.chains)
+    Ly, Lx, D, chi, C = w["Ly"], w["Lx"], w["D"], w["chi"], w["n_chains"]
+    if args.structured:
+        w["tensors"] = inputs.peps_tensors(Ly, Lx, D, w["seed"], inputs.WORKLOADS[args.workload].get("normalise", False),
+                                           bond_decay=1.0)
+    N = Ly * Lx
+    ctx = api.PepsVMC(Ly, Lx, D, chi, C, w["tensors"], w["sketch"], J1=w["J1"], J2=w["J2"], seed=w["seed"],
+                      precision=api.PRECISIONS[args.precision])
+    ctx.set_spins(w["spins"])
+    ctx.sample_sweep(args.therm)
+    start, sweep0 = ctx.get_spins(), ctx.sweep_counter
+    base = dict(study="mixing", workload=args.workload, precision=args.precision, chains=C, sweeps=args.sweeps,
+                therm=args.therm, tensors="structured" if args.structured else "iid")
+    plain = _mixing_arm(ctx, start, sweep0, args.sweeps, N) if "plain" in arms else None
+    if plain:
+        print(json.dumps(dict(arm="plain", **base, **plain)), flush=True)
+    if "learned" not in arms:
+        ctx.close()
+        return
+    ctx.set_spins(start)
+    ctx.set_sweep_counter(sweep0 + 10 ** 6)
+    ctx.set_proposal_params(inputs.proposal_params(w["seed"]))
+    t0 = time.perf_counter()
+    n_train = ctx.proposal_collect(args.collect)
+    t1 = time.perf_counter()
+    loss0 = ctx.proposal_train(1, 256, args.lr)
+    loss = ctx.proposal_train(args.epochs - 1, 256, args.lr) if args.epochs > 1 else loss0
+    t2 = time.perf_counter()
+    ctx.set_spins(start)
+    ctx.amplitude(0)
+    acc = ctx.learned_sweep(4)
+    ctx.set_proposal(1)
+    learned = _mixing_arm(ctx, start, sweep0, args.sweeps, N)
+    print(json.dumps(dict(arm="learned", **base, **learned, train_configs=n_train, collect_s=t1 - t0,
+                          train_s=t2 - t1, loss_first_epoch=loss0, loss_last_epoch=loss,
+                          learned_accept=acc)), flush=True)
+    if plain:
+        dE = learned["E_per_site"] - plain["E_per_site"]
+        sig = float(np.hypot(learned["E_err"], plain["E_err"]))
+        print(json.dumps(dict(summary=True, **base, dE_per_site=dE, dE_sigma=dE / sig if sig > 0 else 0.0,
+                              eff_speedup=learned["eff_samples_per_s"] / plain["eff_samples_per_s"],
+                              raw_speedup=learned["samples_per_s"] / plain["samples_per_s"])), flush=True)
+    ctx.close()
+
+
+def study_cutoff(args):
+    """Convergence in the boundary cutoff Dc (App. D): eps = |Psi_Dc / Psi_ref - 1| and
+    |E_loc,Dc - E_loc,ref| / max(|E_loc,ref|, 1) per configuration against a much larger
+    reference cutoff, on configurations the plain sampler draws at the reference cutoff."""
+    import numpy as np
+
+    from paper_1908_09359_gb300 import api, inputs
+    L, D, C, ref = args.L, args.D, args.chains or 128, args.ref
+    seed = inputs.SEED_BASE + 100 + L
+    t = inputs.peps_tensors(L, L, D, seed, True, bond_decay=1.0 if args.structured else 0.0)
+    sk = inputs.sketch(L, ref, D, seed)
+    prec = api.PRECISIONS[args.precision]
+
+    def measure(chi, spins):
+        ctx = api.PepsVMC(L, L, D, chi, C, t, np.ascontiguousarray(sk[:, :chi, :, :chi]), seed=seed, precision=prec)
+        ctx.set_spins(spins)
+        e, lp, sg = ctx.measure()
+        ctx.close()
+        return e, lp, sg
+
+    ctx = api.PepsVMC(L, L, D, ref, C, t, sk, seed=seed, precision=prec)
+    ctx.set_spins(inputs.start_spins(C, L, L, seed, "random"))
+    ctx.sample_sweep(args.cutoff_sweeps)
+    spins = ctx.get_spins()
+    e_ref, lp_ref, sg_ref = ctx.measure()
+    ctx.close()
+    for chi in [int(x) for x in args.cutoffs.split(",")]:
+        e, lp, sg = measure(chi, spins)
+        eps = np.abs(sg * sg_ref * np.exp(lp - lp_ref) - 1.0)
+        de = np.abs(e - e_ref) / np.maximum(np.abs(e_ref), 1.0)
+        print(json.dumps({"study": "cutoff", "L": L, "D": D, "Dc": chi, "Dc_ref": ref,
+                          "tensors": "structured" if args.structured else "iid", "configs": C,
+                          "eps_median": float(np.median(eps)), "eps_max": float(np.max(eps)),
+                          "dEloc_median": float(np.median(de)), "dEloc_max": float(np.max(de)),
+                          "sign_flips": int(np.sum(sg != sg_ref))}), flush=True)
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.case:
+        run_case(args)
+    elif args.study == "mixing":
+        study_mixing(args)
+    elif args.study == "cutoff":
+        study_cutoff(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -1503,9 +1503,12 @@ struct pepsvmc_ctx {
     if (e != cudaSuccess) return fail_cuda(e);
     if (h) {
       ms(status, 0, sizeof(unsigned));
+      // the environments of a failed call are not valid; the root cause comes first (a
+      // timed-out product leaves garbage behind, a zero amplitude leads to 0/0 later)
+      top_valid = false;
       if (h & ST_TIMEOUT) return fail(PEPSVMC_ETIMEOUT, "device wait budget exhausted");
-      if (h & ST_NONFINITE) return fail(PEPSVMC_ENONFINITE, "non-finite amplitude ratio or environment");
       if (h & ST_ZEROPSI) return fail(PEPSVMC_EZEROPSI, "a configuration with Psi(S) = 0 was met");
+      if (h & ST_NONFINITE) return fail(PEPSVMC_ENONFINITE, "non-finite amplitude ratio or environment");
     }
     return PEPSVMC_OK;
   }

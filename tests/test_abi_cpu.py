@@ -47,7 +47,8 @@ def _cfg(**kw):
 
 @pytest.mark.parametrize("bad", [dict(Ly=3, Lx=3), dict(D=0), dict(chi=0), dict(n_fit=2),
                                  dict(n_chains=0), dict(precision=7), dict(chi=64, D=16),
-                                 dict(chi_measure=-1), dict(chi_measure=65), dict(chi_measure=64, D=16)])
+                                 dict(chi_measure=-1), dict(chi_measure=65), dict(chi_measure=64, D=16),
+                                 dict(chain_offset=-1), dict(wait_budget_cycles=(1 << 62) + 1)])
 def test_invalid_config_is_rejected_before_any_cuda_call(lib, bad):
     cfg = _cfg(**bad)
     t = np.zeros(10)
@@ -74,3 +75,17 @@ def test_null_arguments(lib):
     assert lib.pepsvmc_init(None, None, None, None, None) == _lib.EINVAL
     assert lib.pepsvmc_sample_sweep(None, 1, None) == _lib.EINVAL
     assert lib.pepsvmc_n_params(None) == 0
+    for name in ("pepsvmc_set_wait_budget", "pepsvmc_set_fused"):
+        assert getattr(lib, name)(None, 0) == _lib.EINVAL
+    assert lib.pepsvmc_finalize_sums(None) == _lib.EINVAL
+    assert lib.pepsvmc_get_sums(None, None, None, None) == _lib.EINVAL
+    assert lib.pepsvmc_set_sums(None, None, None, None) == _lib.EINVAL
+    assert lib.pepsvmc_sums_device(None, None, None, None) == _lib.EINVAL
+
+
+def test_config_layout_matches_header():
+    """The ctypes mirror of pepsvmc_config has the C struct's field offsets."""
+    offs = {name: getattr(_lib.Config, name).offset for name, _ in _lib.Config._fields_}
+    assert offs["J1"] == 24 and offs["seed"] == 40 and offs["chi_measure"] == 52
+    assert offs["wait_budget_cycles"] == 56 and offs["chain_offset"] == 64 and offs["reserved"] == 68
+    assert C.sizeof(_lib.Config) == 80

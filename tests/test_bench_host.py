@@ -1,30 +1,45 @@
-"""Host-side arithmetic of bench.py: the binding roofline and the whole-job rate."""
+"""Host-side logic of bench.py: sharding, kernel grouping, whole-job rate, defaults."""
 import os
 import sys
 
+import numpy as np
 import pytest
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import bench  # noqa: E402
 
 
-def test_hbm_roof_binds_below_the_ridge():
-    # 14.8 flop/B against a 578 TFLOP/s compute peak and 6.79 TB/s: ridge 85 flop/B
-    bind, other, inten, ridge = bench.binding_roofline(3.68e14, 2.49e13, 9.77, ("tensor", 578.3, "c"), (6789.6, "h"))
-    assert bind["bound"] == "hbm" and other["bound"] == "tensor"
-    assert inten == pytest.approx(3.68e14 / 2.49e13) and ridge == pytest.approx(578.3e12 / 6789.6e9)
-    assert bind["achieved"] == pytest.approx(2.49e13 / 9.77 / 1e9)
-    assert bind["frac"] == pytest.approx(bind["achieved"] / 6789.6)
-    assert other["achieved"] == pytest.approx(3.68e14 / 9.77 / 1e12)
-
-
-def test_compute_roof_binds_above_the_ridge():
-    bind, other, _, ridge = bench.binding_roofline(1e15, 1e12, 2.0, ("alu", 80.5, "c"), (6789.6, "h"))
-    assert 1e15 / 1e12 > ridge
-    assert bind["bound"] == "alu" and bind["unit"] == "TFLOP/s"
-    assert bind["frac"] == pytest.approx(1e15 / 2.0 / 1e12 / 80.5)
-    assert other["bound"] == "hbm"
-
-
 def test_whole_job_rate_counts_every_rank():
     assert bench.whole_job_rate(4, 512, 2, 10.0) == pytest.approx(4 * 512 * 2 / 10.0)
+
+
+def test_rank_share_slices_one_job():
+    from paper_1908_09359_gb300 import inputs
+    w = dict(inputs.WORKLOADS["peps_8x8"], seed=inputs.SEED_BASE + 1, n_chains=8)
+    parts = [bench.rank_share(w, r, 4) for r in range(4)]
+    whole = bench.rank_share(dict(w, n_chains=32), 0, 1)
+    assert np.array_equal(np.concatenate([p["spins"] for p in parts]), whole["spins"])
+    assert [p["chain_offset"] for p in parts] == [0, 8, 16, 24]
+    assert len({p["key"] for p in parts}) == 1
+
+
+def test_kernel_groups_totals():
+    shapes = [{"shape": "fused4 32 32 32 32", "launches": 2, "flops": 4.0, "ms": 1.0},
+              {"shape": "fused4 8 8 32 32", "launches": 1, "flops": 1.0, "ms": 0.5},
+              {"shape": "gemm tc M256 N32 K256", "launches": 3, "flops": 3.0, "ms": 0.3},
+              {"shape": "qr 256x32", "launches": 5, "flops": 0.0, "ms": 0.2}]
+    g = bench.kernel_groups(shapes)
+    assert g["fused4"] == {"launches": 3, "flops": 5.0, "ms": 1.5}
+    assert g["gemm_tc"]["launches"] == 3 and g["qr"]["ms"] == 0.2
+
+
+def test_default_arguments():
+    a = bench.parse([])
+    assert (a.gpus, a.steps, a.warmup, a.impl, a.precision) == (1, 2, 3, "ours", "bf16x3")
+    assert a.case is None and a.study is None
+
+
+def test_traffic_hash_is_of_the_named_source():
+    t = bench.NCU_TRAFFIC["fused4"]
+    assert os.path.exists(os.path.join(bench.ROOT, t["source"]))
+    assert len(bench.source_sha(t["source"])) == 16
