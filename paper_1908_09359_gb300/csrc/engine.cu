@@ -639,6 +639,49 @@ struct pepsvmc_ctx {
     return f;
   }
 
+  // Fused optimal site of the fit: Y (cV,Dd,cV2) = L (cT,Dl,cV) . T (cT,Du,cT2) . a . R (cT2,Dr,cV2).
+  bool proj_fused_ok(int cT, int cV, int cT2, int cV2, const SiteOp& a) const {
+    return fused_ok(cT, cV, cT2, cV2, a);
+  }
+  cudaError_t fused_proj3(const float* Lf, long long bsL, int cT, int cV, const float* T, long long bsT, int cT2,
+                          const SiteOp& a, const float* Rf, long long bsR, int cV2, float* Y, long long bsY) {
+    Proj3Fused f;
+    f.cT = cT; f.cV = cV; f.cT2 = cT2; f.cV2 = cV2; f.Dl = a.Dl; f.Dr = a.Dr; f.Du = a.Du; f.Dd = a.Dd;
+    f.batch = C;
+    f.L = Lf; f.bsL = bsL; f.sLa = (long long)a.Dl * cV; f.sLl = cV; f.sLv = 1;
+    f.T = T; f.bsT = bsT; f.sTa = (long long)a.Du * cT2; f.sTu = cT2; f.sTa2 = 1;
+    f.A = a.lurd; f.ssA = a.size;
+    f.sAl = (long long)a.Du * a.Dr * a.Dd; f.sAu = (long long)a.Dr * a.Dd; f.sAr = a.Dd; f.sAd = 1;
+    f.sel = (sel_base ? sel_base : spins) + a.spin; f.sel_stride = (long long)Ly * Lx;
+    f.R = Rf; f.bsR = bsR; f.sRa = (long long)a.Dr * cV2; f.sRr = cV2; f.sRv = 1;
+    f.out = Y; f.bsO = bsY; f.sOv = (long long)a.Dd * cV2; f.sOd = cV2; f.sOv2 = 1;
+    f.wait_cycles = wait_budget;
+    const long long b1 = C - 1;
+    if (!span(f.L, b1 * f.bsL + (cT - 1) * f.sLa + (a.Dl - 1) * f.sLl + (cV - 1) * f.sLv, 4, "proj L") ||
+        !span(f.T, b1 * f.bsT + (cT - 1) * f.sTa + (a.Du - 1) * f.sTu + (cT2 - 1) * f.sTa2, 4, "proj T") ||
+        !span(f.A, f.ssA + (a.Dl - 1) * f.sAl + (a.Du - 1) * f.sAu + (a.Dr - 1) * f.sAr + (a.Dd - 1) * f.sAd, 4,
+              "proj A") ||
+        !span(f.R, b1 * f.bsR + (cT2 - 1) * f.sRa + (a.Dr - 1) * f.sRr + (cV2 - 1) * f.sRv, 4, "proj R") ||
+        !span(f.out, b1 * f.bsO + (cV - 1) * f.sOv + (a.Dd - 1) * f.sOd + (cV2 - 1) * f.sOv2, 4, "proj out") ||
+        !span(f.sel, b1 * f.sel_stride, 1, "proj spin selector"))
+      return cudaErrorInvalidValue;
+    ++launches;
+    const double nb = C;
+    const double flops = 2.0 * nb *
+        ((double)a.Dl * cV * a.Du * cT2 * cT + (double)cV * cT2 * a.Dr * a.Dd * a.Dl * a.Du +
+         (double)cV * a.Dd * cV2 * cT2 * a.Dr);
+    if (prof) {
+      prof_acc[0] += 1;
+      prof_acc[1] += flops;
+      prof_acc[5] += 4.0 * ((bsL ? nb : 1.0) * cT * a.Dl * cV + (bsT ? nb : 1.0) * cT * a.Du * cT2 +
+                            (bsR ? nb : 1.0) * cT2 * a.Dr * cV2 + nb * cV * a.Dd * cV2 + 2.0 * a.size);
+    }
+    char key[96];
+    snprintf(key, sizeof(key), "fusedP %d %d %d %d x %d %d %d %d", cT, cV, cT2, cV2, a.Dl, a.Dr, a.Du, a.Dd);
+    const bool split = tc_mode() == 3;
+    return timed(0, [&] { return proj3_fused(f, split, status, st); }, key, flops);
+  }
+
   // Three-line left step (App. C, Fig. "contraction" (c)): E (cT,Dl,cB) -> out (cT2,Dr,cB2).
   cudaError_t left3(const float* E, long long bsE, int cT, int cB, const float* T, long long bsT, int cT2,
                     const SiteOp& a, int flip, const float* B, long long bsB, int cB2, float* out,
@@ -994,11 +1037,23 @@ struct pepsvmc_ctx {
           const float* Rin = m == L - 1 ? ones : envRp(m + 1);
           const long long bsR = m == L - 1 ? 1 : S;
           float* Vs = Vb + m * vss;
-          PV_CUDA(proj3(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], Rin, bsR,
-                        vb[m + 1], Vs, S));
+          // fused: the optimal site in one kernel, then the new left environment as a full
+          // three-line step with the fitted site as the bottom MPS (its first two products
+          // are not kept on chip between the two kernels)
+          const bool fz = proj_fused_ok(tb[m], vb[m], tb[m + 1], vb[m + 1], a[m]);
+          if (fz)
+            PV_CUDA(fused_proj3(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], Rin, bsR,
+                                vb[m + 1], Vs, S));
+          else
+            PV_CUDA(proj3(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], Rin, bsR,
+                          vb[m + 1], Vs, S));
           if (m < L - 1) {
             PV_CUDA(qr(Vs, S, vb[m + 1], 1, Vs, S, vb[m + 1], 1, vb[m] * p[m], vb[m + 1], C));
-            PV_CUDA(left3_tail_after_proj(a[m], vb[m], tb[m + 1], Vs, S, vb[m + 1], envLp(m + 1), S));
+            if (fz)
+              PV_CUDA(left3(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], 0, Vs, S,
+                            vb[m + 1], envLp(m + 1), S));
+            else
+              PV_CUDA(left3_tail_after_proj(a[m], vb[m], tb[m + 1], Vs, S, vb[m + 1], envLp(m + 1), S));
             PV_CUDA(norm2(envLp(m + 1), S, tb[m + 1] * a[m].Dr * vb[m + 1], nullptr, 0, nullptr, 0, exps));
           }
         }
@@ -1009,12 +1064,21 @@ struct pepsvmc_ctx {
           const float* Rin = m == L - 1 ? ones : envRp(m + 1);
           const long long bsR = m == L - 1 ? 1 : S;
           float* Vs = Vb + m * vss;
-          PV_CUDA(proj3_right(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], Rin,
-                              bsR, vb[m + 1], Vs, S));
+          const bool fz = proj_fused_ok(tb[m], vb[m], tb[m + 1], vb[m + 1], a[m]);
+          if (fz)
+            PV_CUDA(fused_proj3(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], Rin, bsR,
+                                vb[m + 1], Vs, S));
+          else
+            PV_CUDA(proj3_right(Lin, bsL, tb[m], vb[m], Tin.site(m), Tin.chain_stride, tb[m + 1], a[m], Rin,
+                                bsR, vb[m + 1], Vs, S));
           if (m > 0) {
             const int rows = p[m] * vb[m + 1];
             PV_CUDA(qr(Vs, S, 1, rows, Vs, S, 1, rows, rows, vb[m], C));
-            PV_CUDA(right3_tail(a[m], tb[m], vb[m + 1], Vs, S, vb[m], envRp(m), S));
+            if (fz)
+              PV_CUDA(right3(Rin, bsR, tb[m + 1], vb[m + 1], Tin.site(m), Tin.chain_stride, tb[m], a[m], 0, Vs, S,
+                             vb[m], envRp(m), S));
+            else
+              PV_CUDA(right3_tail(a[m], tb[m], vb[m + 1], Vs, S, vb[m], envRp(m), S));
             PV_CUDA(norm2(envRp(m), S, tb[m] * a[m].Dl * vb[m]));
           }
         }

@@ -91,3 +91,42 @@ inline bool env4_fused_fits(const Env4Fused& f) {
 cudaError_t env4_fused(const Env4Fused& a, bool split, unsigned* status, cudaStream_t st);
 
 }  // namespace pv
+
+namespace pv {
+
+// Optimal site of the variational fit (App. B): the boundary MPS site that best fits
+// M_k |U> given its left and right environments, for every chain c:
+//   Y[c](v,d,v') = sum over a,l,a',u,r of L[c](a,l,v) T[c](a,u,a') A_s(l,u,r,d) R[c](a',r,v')
+// as three products in one kernel (L.T over a, .A over (l,u), .R over (a',r), the last
+// accumulated over tiles of a'), intermediates on chip.
+struct Proj3Fused {
+  int cT = 0, cV = 0, cT2 = 0, cV2 = 0, Dl = 0, Dr = 0, Du = 0, Dd = 0;
+  int batch = 0;
+  const float* L = nullptr;  // L(a,l,v) = L[c*bsL + a*sLa + l*sLl + v*sLv]
+  long long bsL = 0, sLa = 0, sLl = 0, sLv = 0;
+  const float* T = nullptr;  // T(a,u,a') = T[c*bsT + a*sTa + u*sTu + a'*sTa2]
+  long long bsT = 0, sTa = 0, sTu = 0, sTa2 = 0;
+  const float* A = nullptr;  // A_s(l,u,r,d) = A[s*ssA + l*sAl + u*sAu + r*sAr + d*sAd]
+  long long ssA = 0, sAl = 0, sAu = 0, sAr = 0, sAd = 0;
+  const int8_t* sel = nullptr;
+  long long sel_stride = 0;
+  const float* R = nullptr;  // R(a',r,v') = R[c*bsR + a'*sRa + r*sRr + v'*sRv]
+  long long bsR = 0, sRa = 0, sRr = 0, sRv = 0;
+  float* out = nullptr;      // Y(v,d,v') = out[c*bsO + v*sOv + d*sOd + v'*sOv2]
+  long long bsO = 0, sOv = 0, sOd = 0, sOv2 = 0;
+  long long wait_cycles = 0;
+};
+
+inline bool proj3_fused_fits(const Proj3Fused& f) {
+  const int x[4] = {f.cT, f.cV, f.cT2, f.cV2};
+  const int d[4] = {f.Dl, f.Dr, f.Du, f.Dd};
+  for (int v : x)
+    if (v < 1 || v > kFusedChi) return false;
+  for (int v : d)
+    if (v < 1 || v > kFusedD) return false;
+  return true;
+}
+
+cudaError_t proj3_fused(const Proj3Fused& a, bool split, unsigned* status, cudaStream_t st);
+
+}  // namespace pv

@@ -12,12 +12,16 @@
 // accumulators are drained after each product by the epilogue warps, split into BF16
 // hi + lo and stored, re-indexed, as the next product's A operand (S2's in the 128-byte
 // swizzled layout, S3's and S4's without swizzle; in every case the eight lanes that write
-// one row group hit eight different bank groups).  X, Y and Z share one buffer (each is
-// dead once its product completed) and S3 reuses S1's accumulator columns.  The E and B
-// slices of the next b tile are fetched into registers while the current tile computes.
-// Bonds below the maxima are zero-padded on chip.  Shared memory 93 KB and 256 tensor-
-// memory columns per CTA: two CTAs share an SM, so one CTA's epilogues overlap the
-// other's products.
+// one row group hit eight different bank groups).  X, Y and Z share one buffer and S1, S2
+// and S3 one accumulator region (each is dead once the next product was issued).
+// Split BF16 needs three BF16 products per step; an MMA instruction costs about the same
+// for any N up to 128, so S1-S3 issue A_hi x [B_hi | B_lo] as one MMA of twice the width
+// plus A_lo x B_hi, and the epilogue adds the two column halves (the lo copy of each B
+// tile directly follows its hi copy with the same row-group stride).  The E and B slices
+// of the next b tile are fetched into registers while the current tile computes.  Bonds
+// below the maxima are zero-padded on chip.  Shared memory 93 KB and 256 tensor-memory
+// columns per CTA: two CTAs share an SM, so one CTA's epilogues overlap the other's
+// products.
 #include "fused.cuh"
 #include "tc_util.cuh"
 
@@ -39,7 +43,7 @@ constexpr uint32_t SZ_B = 32 * 32, OFF_B = OFF_A2 + 2 * SZ_A2;      // S4 B, two
 constexpr uint32_t SMEM_USED = OFF_B + 4 * SZ_B;
 constexpr uint32_t SMEM_BYTES = SMEM_USED + 1024;
 constexpr uint32_t TMEM_COLS = 256;
-constexpr uint32_t COL_S1 = 0, COL_S2 = 64, COL_S3 = 0, COL_S4 = 128;
+constexpr uint32_t COL_S123 = 0, COL_S4 = 128;
 static_assert(2 * (SMEM_BYTES + 1024) <= 233472, "two fused four-line CTAs must fit one SM");
 
 __device__ __forceinline__ bool block_wait(uint64_t* bar, uint32_t parity, long long budget) {
@@ -54,6 +58,31 @@ __device__ __forceinline__ void issue3(uint32_t d, uint64_t a_hi, uint64_t a_lo,
   if constexpr (X3) {
     mma<2>(d, a_hi, b_lo, id, 1u);
     mma<2>(d, a_lo, b_hi, id, 1u);
+  }
+}
+
+// One K step of a split (or plain) BF16 product into accumulator d (N columns; with X3
+// columns N..2N-1 receive A_hi x B_lo).
+template <bool X3>
+__device__ __forceinline__ void mma_merged(uint32_t d, uint64_t a_hi, uint64_t a_lo, uint64_t b, uint32_t id_n,
+                                           uint32_t id_2n, uint32_t acc) {
+  if constexpr (X3) {
+    mma<2>(d, a_hi, b, id_2n, acc);
+    mma<2>(d, a_lo, b, id_n, 1u);
+  } else {
+    mma<2>(d, a_hi, b, id_n, acc);
+  }
+}
+
+// 32 accumulator columns of this thread's row, the split halves added (X3).
+template <bool X3>
+__device__ __forceinline__ void load_acc(uint32_t taddr, float* v) {
+  tmem_ld32(taddr, v);
+  if constexpr (X3) {
+    float w[32];
+    tmem_ld32(taddr + 64, w);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] += w[i];
   }
 }
 
@@ -166,6 +195,7 @@ __global__ void __launch_bounds__(kThreads, 2) env4_fused_kernel(const Env4Fused
   const uint32_t tmem = tmem_base;
   const int q = warp & 3, h = warp >> 2;
   const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+  const uint32_t id_n = idesc<2>(128, 64), id_2n = idesc<2>(128, 128);
   bool ok = true;
   int failed = -1;
   uint32_t fphase = 0;
@@ -177,11 +207,10 @@ __global__ void __launch_bounds__(kThreads, 2) env4_fused_kernel(const Env4Fused
     // ---- S1
     if (tid == 0) {
       tc_after_sync();
-      const uint32_t id = idesc<2>(128, 64);
       for (int ks = 0; ks < 2; ++ks) {
         const uint32_t ao = sbase + OFF_E + ks * 256, bo = sbase + OFF_T + ks * 256;
-        issue3<X3>(tmem + COL_S1, sdesc(ao, 128, 512), sdesc(ao + SZ_E, 128, 512), sdesc(bo, 128, 512),
-                   sdesc(bo + SZ_T, 128, 512), id, ks > 0 ? 1u : 0u);
+        mma_merged<X3>(tmem + COL_S123, sdesc(ao, 128, 512), sdesc(ao + SZ_E, 128, 512), sdesc(bo, 128, 512), id_n,
+                       id_2n, ks > 0 ? 1u : 0u);
       }
       commit(&bar[0]);
     }
@@ -190,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 2) env4_fused_kernel(const Env4Fused
     {  // S1 epilogue: row (b,l2,l1) -> S2 rows (l2,b,a'), chunk l1
       const int m1 = q * 32 + lane, bl = m1 >> 6, l2 = (m1 >> 3) & 7, l1 = m1 & 7;
       float v[32];
-      tmem_ld32(tmem + lane_base + COL_S1 + h * 32, v);
+      load_acc<X3>(tmem + lane_base + COL_S123 + h * 32, v);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
         put16<2, X3>(sm + OFF_W + sw128_chunk_off(l2 * 16 + bl * 8 + h * 4 + i, l1), v + i * 8, SZ_W);
@@ -203,11 +232,10 @@ __global__ void __launch_bounds__(kThreads, 2) env4_fused_kernel(const Env4Fused
     // ---- S2
     if (tid == 0) {
       tc_after_sync();
-      const uint32_t id = idesc<2>(128, 64);
       for (int ks = 0; ks < 4; ++ks) {
         const uint32_t ao = sbase + OFF_W + ks * 32, bo = sbase + OFF_A1 + ks * 256;
-        issue3<X3>(tmem + COL_S2, sdesc_sw128(ao), sdesc_sw128(ao + SZ_W), sdesc(bo, 128, 1024),
-                   sdesc(bo + SZ_A1, 128, 1024), id, ks > 0 ? 1u : 0u);
+        mma_merged<X3>(tmem + COL_S123, sdesc_sw128(ao), sdesc_sw128(ao + SZ_W), sdesc(bo, 128, 1024), id_n, id_2n,
+                       ks > 0 ? 1u : 0u);
       }
       commit(&bar[1]);
     }
@@ -216,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 2) env4_fused_kernel(const Env4Fused
     {  // S2 epilogue: row (l2,b,a') -> S3 rows (b,r1,a'), chunk l2
       const int m2 = q * 32 + lane, l2 = m2 >> 4, bl = (m2 >> 3) & 1, al = m2 & 7;
       float v[32];
-      tmem_ld32(tmem + lane_base + COL_S2 + h * 32, v);
+      load_acc<X3>(tmem + lane_base + COL_S123 + h * 32, v);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
         put16<2, X3>(sm + OFF_W + kmajor_off(bl * 64 + (h * 4 + i) * 8 + al, l2 * 8, 8), v + i * 8, SZ_W);
@@ -227,11 +255,10 @@ __global__ void __launch_bounds__(kThreads, 2) env4_fused_kernel(const Env4Fused
     // ---- S3
     if (tid == 0) {
       tc_after_sync();
-      const uint32_t id = idesc<2>(128, 64);
       for (int ks = 0; ks < 4; ++ks) {
         const uint32_t ao = sbase + OFF_W + ks * 256, bo = sbase + OFF_A2 + ks * 256;
-        issue3<X3>(tmem + COL_S3, sdesc(ao, 128, 1024), sdesc(ao + SZ_W, 128, 1024), sdesc(bo, 128, 1024),
-                   sdesc(bo + SZ_A2, 128, 1024), id, ks > 0 ? 1u : 0u);
+        mma_merged<X3>(tmem + COL_S123, sdesc(ao, 128, 1024), sdesc(ao + SZ_W, 128, 1024), sdesc(bo, 128, 1024), id_n,
+                       id_2n, ks > 0 ? 1u : 0u);
       }
       commit(&bar[2]);
     }
@@ -240,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 2) env4_fused_kernel(const Env4Fused
     {  // S3 epilogue: row (b,r1,a') -> S4 rows (r1,r2,a'), chunk b
       const int m3 = q * 32 + lane, bl = m3 >> 6, r1 = (m3 >> 3) & 7, al = m3 & 7;
       float v[32];
-      tmem_ld32(tmem + lane_base + COL_S3 + h * 32, v);
+      load_acc<X3>(tmem + lane_base + COL_S123 + h * 32, v);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
         put16<2, X3>(sm + OFF_W + kmajor_off(r1 * 64 + (h * 4 + i) * 8 + al, bl * 8, 2), v + i * 8, SZ_W);
@@ -314,6 +341,8 @@ cudaError_t launch(const Env4Fused& a, unsigned* status, cudaStream_t st) {
   if (!configured) {
     PV_CUDA(cudaFuncSetAttribute(env4_fused_kernel<X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)SMEM_BYTES));
+    // the whole shared memory for this kernel, so that two CTAs fit an SM
+    PV_CUDA(cudaFuncSetAttribute(env4_fused_kernel<X3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     configured = true;
   }
   const long long blocks = (long long)a.batch * ((a.cT2 + kAT - 1) / kAT);
