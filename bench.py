@@ -20,7 +20,8 @@ step of every rank.  Rank 0 prints one JSON line.
 
 Measurement helpers (not part of the timed line):
     python bench.py --case env3|env4|step   one launch shape or one profiled step
-    python bench.py --study mixing|cutoff    plain vs learned sampler; convergence in Dc
+    python bench.py --study mixing|cutoff|nnasp    plain vs learned sampler; convergence in Dc;
+                                                  random-NNASP vs sequential sweep
 """
 from __future__ import annotations
 
@@ -42,12 +43,17 @@ UNIT = "samples/s"
 # FP32 CUDA-core peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# DRAM traffic of one bulk launch of the fused four-line step (Dc 32, D 8, 512 chains),
-# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the kernel whose
-# source hashed to `source_sha`; the bench reports it only while the source is unchanged.
+# DRAM traffic of one bulk launch of each fused step (Dc 32, D 8), dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the kernel whose source hashed to
+# `source_sha`, per chain of that capture; the bench reports it only while the source is
+# unchanged.
 NCU_TRAFFIC = {
-    "fused4": {"bytes_per_launch": None, "chains": 512, "source": "paper_1908_09359_gb300/csrc/fused_env4.cu",
-               "source_sha": None, "summary": "profiles/fused4_env4_bulk_peps24x24.md"},
+    "fused4": {"bytes_per_chain": (167.906304e6 + 91.586304e6) / 512,
+               "source": "paper_1908_09359_gb300/csrc/fused_env4.cu", "source_sha": "2cb0277a6c9307e6",
+               "summary": "profiles/fused4_env4_bulk_peps24x24.md"},
+    "fused3": {"bytes_per_chain": (201.427456e6 + 45.492992e6) / 2048,
+               "source": "paper_1908_09359_gb300/csrc/fused_env3.cu", "source_sha": "1b8d8fc64503cdc2",
+               "summary": "profiles/fused3_env3_bulk_peps24x24.md"},
 }
 
 
@@ -74,7 +80,7 @@ def parse(argv=None):
     p.add_argument("--reps", type=int, default=10)
     p.add_argument("--separate", action="store_true", help="--case env3/env4: three/four separate products")
     p.add_argument("--top", type=int, default=25)
-    p.add_argument("--study", choices=["mixing", "cutoff"], default=None)
+    p.add_argument("--study", choices=["mixing", "cutoff", "nnasp"], default=None)
     p.add_argument("--structured", action="store_true", help="bond spectra exp(-i) instead of iid tensors")
     p.add_argument("--therm", type=int, default=50)
     p.add_argument("--sweeps", type=int, default=200)
@@ -569,8 +575,8 @@ def run_ours(args):
         achieved = per_launch_flops / (per_launch_ms / 1e3) / 1e12
         traffic = None
         t = NCU_TRAFFIC.get(dominant)
-        if t and rec is bulk and t["bytes_per_launch"] and t["source_sha"] == source_sha(t["source"]):
-            traffic = t["bytes_per_launch"] * C / t["chains"]
+        if t and rec is bulk and t["source_sha"] == source_sha(t["source"]):
+            traffic = t["bytes_per_chain"] * C
         step_flops = prof["gemm_flops"]
         roofline = {
             "kernel": {"fused4": "env4_fused_kernel (four-line column step, tcgen05, split BF16)",
@@ -686,7 +692,8 @@ def run_case(args):
         A1, A2 = r(2, D, D, D, D), r(2, D, D, D, D)
         out = torch.empty(n, chi, D, D, chi, device="cuda")
         dims = (n, chi, chi, chi, chi, D, D, D, D, D, D, D)
-        run = lambda: ctx.env4_left(E, T, A1, spins, A2, spins, B, out, dims)  # noqa: E731
+        # the engine's own layout of four-line environments when its steps are fused
+        run = lambda: ctx.env4_left(E, T, A1, spins, A2, spins, B, out, dims, bmajor=not args.separate)  # noqa: E731
         flops = 2.0 * (2 * chi ** 3 * D ** 3 + 2 * chi ** 2 * D ** 5) * n
     for _ in range(3):
         run()
@@ -782,6 +789,55 @@ def study_mixing(args):
     ctx.close()
 
 
+def study_nnasp(args):
+    """The paper's check of the sequential sweep (Sec. II A, Fig. SweepScheme): the random
+    NNASP scheme (N uniformly chosen antiparallel-pair attempts per sweep, Eq. (prob_r))
+    and the sequential sweep run from the same thermalised configurations; per scheme E
+    per site with its tau-corrected error, tau_int of E_loc and M_z^2, sweeps/s and
+    effective samples/s, and the difference of the two energies in units of its error."""
+    import numpy as np
+
+    from paper_1908_09359_gb300 import api, autocorr, inputs
+    w = inputs.workload(args.workload, n_chains=args.chains)
+    Ly, Lx, D, chi, C = w["Ly"], w["Lx"], w["D"], w["chi"], w["n_chains"]
+    if args.structured:
+        w["tensors"] = inputs.peps_tensors(Ly, Lx, D, w["seed"], inputs.WORKLOADS[args.workload].get("normalise", False),
+                                           bond_decay=1.0)
+    N = Ly * Lx
+    ctx = api.PepsVMC(Ly, Lx, D, chi, C, w["tensors"], w["sketch"], J1=w["J1"], J2=w["J2"], seed=w["seed"],
+                      precision=api.PRECISIONS[args.precision])
+    ctx.set_spins(w["spins"])
+    ctx.sample_sweep(args.therm)
+    start, sweep0 = ctx.get_spins(), ctx.sweep_counter
+    base = dict(study="nnasp", workload=args.workload, precision=args.precision, chains=C, sweeps=args.sweeps,
+                therm=args.therm, tensors="structured" if args.structured else "iid")
+    out = {}
+    for scheme in ("sequential", "random"):
+        ctx.set_spins(start)
+        ctx.set_sweep_counter(sweep0)
+        el, mz, secs = np.empty((args.sweeps, C)), np.empty((args.sweeps, C)), 0.0
+        for t in range(args.sweeps):
+            t0 = time.perf_counter()
+            (ctx.sample_sweep if scheme == "sequential" else ctx.random_sweep)(1)
+            e, _, _ = ctx.measure()
+            secs += time.perf_counter() - t0
+            el[t] = e
+            mz[t] = autocorr.staggered_mz2(ctx.get_spins())
+        mean, err = autocorr.mean_and_error(el / N)
+        tau = max(autocorr.tau_int(el)[0], autocorr.tau_int(mz)[0])
+        sps = args.sweeps * C / secs
+        out[scheme] = dict(E_per_site=mean, E_err=err, tau_eloc=autocorr.tau_int(el)[0],
+                           tau_mz2=autocorr.tau_int(mz)[0], Mz2=float(mz.mean()), samples_per_s=sps,
+                           eff_samples_per_s=sps / (2 * tau))
+        print(json.dumps(dict(scheme=scheme, **base, **out[scheme])), flush=True)
+    d = out["random"]["E_per_site"] - out["sequential"]["E_per_site"]
+    sig = float(np.hypot(out["random"]["E_err"], out["sequential"]["E_err"]))
+    print(json.dumps(dict(summary=True, **base, dE_per_site=d, dE_sigma=d / sig if sig > 0 else 0.0,
+                          eff_ratio_sequential_over_random=out["sequential"]["eff_samples_per_s"]
+                          / out["random"]["eff_samples_per_s"])), flush=True)
+    ctx.close()
+
+
 def study_cutoff(args):
     """Convergence in the boundary cutoff Dc (App. D): eps = |Psi_Dc / Psi_ref - 1| and
     |E_loc,Dc - E_loc,ref| / max(|E_loc,ref|, 1) per configuration against a much larger
@@ -827,6 +883,8 @@ def main(argv=None):
         study_mixing(args)
     elif args.study == "cutoff":
         study_cutoff(args)
+    elif args.study == "nnasp":
+        study_nnasp(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

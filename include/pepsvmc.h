@@ -69,7 +69,17 @@ typedef struct {
                         /* (>= 0): a job whose chains are split over several */
                         /* contexts draws the same numbers as one context   */
                         /* holding all of them                              */
-  int32_t reserved[3];  /* must be zero                                    */
+  int32_t symmetrize;   /* 0: sample |Psi|^2.  1: spin-inversion symmetrised */
+                        /* Phi(S) = Psi(S) + Psi(S-bar), S-bar = all spins   */
+                        /* reversed (end of Sec. II B): n_chains must be     */
+                        /* even, chain p + n_chains/2 holds S-bar of chain p */
+                        /* (pairs p = 0 .. n_chains/2 - 1), the sequential   */
+                        /* sweep samples |Phi|^2 (one decision per pair, the */
+                        /* uniform of Philox chain word chain_offset + p),   */
+                        /* and the accumulated sums of pepsvmc_energy_and_grad */
+                        /* take E^Phi and G^Phi of each pair as one sample.  */
+                        /* Random-NNASP and learned sweeps return EINVAL.   */
+  int32_t reserved[2];  /* must be zero                                    */
 } pepsvmc_config;
 
 /* Create a context (on failure *out may still receive a context that holds the
@@ -82,7 +92,8 @@ typedef struct {
  *            X = max(chi, chi_measure), copied; a fit with cutoff c uses the
  *            leading [c][D][c] corner of each site.
  *   stream:  a cudaStream_t (NULL = the legacy default stream).
- * All chains start in the Neel configuration; use pepsvmc_set_spins to change.
+ * All chains start in the Neel configuration (with symmetrize, chains
+ * n_chains/2 .. n_chains-1 in its inversion); use pepsvmc_set_spins to change.
  * Errors: EINVAL (bad config), ENOMEM, ECUDA.                               */
 int pepsvmc_init(const pepsvmc_config* cfg, const double* tensors, const double* sketch,
                  void* stream, pepsvmc_ctx** out);
@@ -124,6 +135,21 @@ uint64_t pepsvmc_get_sweep_counter(const pepsvmc_ctx* ctx);
  * Errors: EZEROPSI, ENONFINITE, ECUDA.                                      */
 int pepsvmc_sample_sweep(pepsvmc_ctx* ctx, int32_t n_sweeps, double* accept_rate_out);
 
+/* n_sweeps sweeps of the random-NNASP scheme (Sec. II A, Eq. (prob_r)), the paper's
+ * reference for the sequential sweep: a sweep is N = Ly*Lx attempts; each picks one of
+ * the K_a antiparallel nearest-neighbour pairs of a chain's configuration uniformly
+ * (pairs listed in the bond order of pepsvmc_sample_sweep; index floor(r K_a) with r from
+ * word 0 of Philox (chain + chain_offset, sweep, attempt, "RAND")), swaps it, and accepts
+ * with r' < min[1, |Psi_b|^2 K_a / (|Psi_a|^2 K_b)] (r' from word 1).  Every Psi is a full
+ * boundary-MPS contraction at chi closed at row Ly/2, so an attempt costs a whole
+ * amplitude: O(N^2 D^4 Dc^2) per sweep instead of the sequential sweep's O(N D^4 Dc^2).
+ *   accept_rate_out: nullable host double, accepted / proposed over the call.
+ * pepsvmc_get_random_trace: per [chain][attempt] of the last sweep (tracing on): the bond
+ * id swapped (-1: no antiparallel pair), Psi_b/Psi_a, decision (-1, 0, 1); all nullable.
+ * Errors: EZEROPSI, ENONFINITE, ECUDA; ESTATE (trace) without a traced sweep.        */
+int pepsvmc_random_sweep(pepsvmc_ctx* ctx, int32_t n_sweeps, double* accept_rate_out);
+int pepsvmc_get_random_trace(pepsvmc_ctx* ctx, int32_t* bond, double* ratio, int8_t* decision);
+
 /* Per-proposal record of the most recent sweep (after pepsvmc_enable_trace(ctx,1)):
  *   ratio:    host float64 [n_chains][2*Lx*Ly - Lx - Ly], Psi(S_b)/Psi(S_a)
  *   decision: host int8 same shape: -1 no proposal (parallel pair), 0 rejected,
@@ -142,6 +168,19 @@ int pepsvmc_get_trace(pepsvmc_ctx* ctx, double* ratio, int8_t* decision);
  * Errors: EZEROPSI, ENONFINITE, ECUDA.                                      */
 int pepsvmc_measure(pepsvmc_ctx* ctx, double* eloc, double* logpsi, int8_t* sign);
 
+/* Symmetrised results of the last measurement (pepsvmc_measure or a step of
+ * pepsvmc_energy_and_grad) of a context created with symmetrize = 1, per
+ * pair p (host float64, n_chains/2 entries each, nullable):
+ *   w:        Psi(S-bar)/Psi(S) = sign_{p+P} sign_p exp(lnPsi_{p+P} - lnPsi_p)
+ *             from the measured amplitudes of chains p and p + P;
+ *   eloc_phi: E^Phi(S) = (E_loc(S) + w E_loc(S-bar)) / (1 + w), the local
+ *             energy of Phi (H commutes with the global spin inversion, so
+ *             <S|H|S'> = <S-bar|H|S'-bar>).
+ * The gradient sums use G^Phi(S) = (G(S) + w G(S-bar)) / (1 + w), with G(S) in
+ * the slots of S and G(S-bar) in the opposite slots.
+ * Errors: ESTATE (no symmetrize, or no measurement yet), ECUDA.             */
+int pepsvmc_get_phi(pepsvmc_ctx* ctx, double* eloc_phi, double* w);
+
 /* G(S) of one chain from the last measurement: host float64, packed layout of
  * ONE spin slot per site, i.e. sum over sites of Dl*Dr*Du*Dd entries, each
  * site (l, r, u, d) row-major; it belongs to slot s(k,m) of that chain.     */
@@ -156,7 +195,9 @@ int pepsvmc_amplitude(pepsvmc_ctx* ctx, int32_t row, double* logpsi, int8_t* sig
  * accumulating E_tot, P1 = sum G E_loc and P2 = sum G over all chains and
  * sweeps in float64.  Outputs (host, nullable):
  *   E_mean, E_var:   mean and variance of E_loc over the n_sweeps*n_chains samples
- *   eloc, logpsi, sign: per sample [sweep][chain]
+ *                    (with symmetrize: of E^Phi over the n_sweeps*n_chains/2 pairs)
+ *   eloc, logpsi, sign: per sample [sweep][chain] (with symmetrize, eloc holds
+ *                    E^Phi of the chain's pair)
  *   grad:            dE/dA = <G E_loc> - <G><E_loc> (Eq. (5), without the
  *                    factor 2 of the exact derivative), packed layout.
  * Errors: as pepsvmc_sample_sweep and pepsvmc_measure.                       */
@@ -216,13 +257,17 @@ int pepsvmc_env3_left(pepsvmc_ctx* ctx, const float* E, const float* T, const fl
  * slot in the order (l, u, r, d) (A2's up leg is A1's down leg, Dd1); chain c uses slot 1
  * of A1 when spins1[c] < 0 and of A2 when spins2[c] < 0 (int8 device arrays), slot 0
  * otherwise or when the pointer is NULL.  In the tensor-core precisions bonds up to
- * Dc = 32 and D = 8 run as one fused kernel.  Asynchronous on the stream.
- * Errors: EINVAL (null pointers, non-positive sizes, more chains than the context's or
- * intermediates larger than its scratch); ECUDA.                                     */
+ * Dc = 32 and D = 8 run as one fused kernel.  bmajor = 1 stores E and out b-major instead,
+ * E(a,l1,l2,b) at [b][a][l1][l2] and out(a',r1,r2,b') at [b'][a'][r1][r2] (the order the
+ * context keeps its own four-line environments in when its steps are fused; the fused
+ * kernel only).  Asynchronous on the stream.
+ * Errors: EINVAL (null pointers, non-positive sizes, more chains than the context's,
+ * intermediates larger than its scratch, bmajor not 0 or 1, or bmajor without the fused
+ * kernel); ECUDA.                                                                      */
 int pepsvmc_env4_left(pepsvmc_ctx* ctx, const float* E, const float* T, const float* A1, const int8_t* spins1,
                       const float* A2, const int8_t* spins2, const float* B, float* out, int32_t n_chains,
                       int32_t cT, int32_t cB, int32_t cT2, int32_t cB2, int32_t D1l, int32_t D1r, int32_t Du1,
-                      int32_t Dd1, int32_t D2l, int32_t D2r, int32_t Dd2);
+                      int32_t Dd1, int32_t D2l, int32_t D2r, int32_t Dd2, int32_t bmajor);
 
 /* pepsvmc_env3_left without a context and without allocating anything (the paper
  * has no counterpart; this is a library convenience).  For callers that cannot
@@ -234,9 +279,10 @@ int pepsvmc_env4_left(pepsvmc_ctx* ctx, const float* E, const float* T, const fl
  * Scratch: the two intermediates live in one fixed array of
  * PEPSVMC_NOALLOC_SCRATCH_FLOATS floats (16 MiB) of the library's own device
  * memory, present on every GPU where the library's device code is loaded until
- * the process exits.  The first call on a device looks up that array's device
- * address (with the device current); make that first call before any stream
- * capture.  Every call uses the same array, and it keeps the last call's
+ * the process exits.  Every call looks up that array's device address for the
+ * current device and context (no allocation; after a device reset the new
+ * context's address is used); the first call on a device loads the library's
+ * device code there, so make that first call before any stream capture.  Every call uses the same array, and it keeps the last call's
  * contents (nothing in it needs to start at zero); calls whose execution overlaps
  * on the GPU -- on different streams or devices sharing nothing, or from several
  * host threads -- race on it and must be serialised by the caller.

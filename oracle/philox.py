@@ -14,6 +14,8 @@ The method draws two kinds of uniforms from it (both sides use the same counters
   counter = (chain, sweep, bond, TAG_METROPOLIS).
 * Sign-SGD step (Sec. II B, Eq. (10)): counter = (element & 0xffffffff,
   element >> 32, step, TAG_UPDATE).
+* Random-NNASP attempt (Sec. II A, Eq. (prob_r)): counter = (chain, sweep, attempt,
+  TAG_RANDOM); word 0 picks the pair, word 1 is the acceptance uniform.
 
 The uniform is r = (word0 >> 8) * 2**-24, exactly representable in float32.
 """
@@ -29,6 +31,7 @@ MASK = 0xFFFFFFFF
 
 TAG_METROPOLIS = 0x4D455452  # "METR"
 TAG_UPDATE = 0x55504454      # "UPDT"
+TAG_RANDOM = 0x52414E44      # "RAND"
 
 
 def philox4x32_10(ctr, key):
@@ -80,3 +83,16 @@ def update_uniforms(seed: int, step: int, n: int) -> np.ndarray:
     e = np.arange(n, dtype=np.uint64)
     w0, _, _, _ = philox4x32_10_np(e & np.uint64(MASK), e >> np.uint64(32), step, TAG_UPDATE, k0, k1)
     return uniform24(w0)
+
+
+def random_attempt_words(seed: int, chain: int, sweep: int, attempt: int):
+    """(pick word, acceptance uniform) of one random-NNASP attempt."""
+    k0, k1 = key_of(seed)
+    w = philox4x32_10((chain, sweep, attempt, TAG_RANDOM), (k0, k1))
+    return int(w[0]), float(uniform24(w[1]))
+
+
+def pick(word: int, n: int) -> int:
+    """Index in [0, n) from the top 24 bits of a word: floor(r n) with r = (word >> 8) 2^-24,
+    in integer arithmetic so that both sides agree exactly."""
+    return ((word >> 8) * n) >> 24

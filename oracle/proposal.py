@@ -6,7 +6,7 @@ nearest-neighbour swaps (Sec. II A) and names machine learning only as an outloo
 with min[1, |Psi(S')|^2 q(S|S') / (|Psi(S)|^2 q(S'|S))], which the paper's K_a/K_b
 factors instantiate for uniformly chosen pairs -- with a learned q.
 
-Readings (listed in the design notes):
+Readings of points the paper leaves open:
 * Network: three 3x3 convolutions with zero padding on the +-1 spin grid,
   1 -> 32 -> 32 -> 2 channels, ReLU after the first two.  Output channel 0 at (k, m)
   is the logit of the horizontal bond (k,m)-(k,m+1), channel 1 that of the vertical

@@ -11,13 +11,15 @@ min[1, |Psi(S')|^2 / |Psi(S)|^2].
 
 This module writes both schemes as exact transition matrices over the S^z = 0 sector
 of a small lattice, for any amplitude function, so that their stationary
-distributions can be compared with |Psi|^2 and with each other.
+distributions can be compared with |Psi|^2 and with each other; and the random scheme
+as a sampler on the boundary-MPS amplitude (App. B) with Philox uniforms, one sweep being
+N attempts (N = Ly Lx, Sec. II A), which the GPU sampler reproduces draw for draw.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import exact
+from . import exact, philox, vmc
 
 
 def nn_bonds(Ly, Lx):
@@ -95,3 +97,61 @@ def sector(grid):
     Ly, Lx = len(grid), len(grid[0])
     cfg = exact.sz0_configs(Ly, Lx)
     return cfg, np.array([exact.amplitude_transfer(grid, c) for c in cfg])
+
+
+def boundary_psi(grid, spins, chi, W, n_fit):
+    """(ln|Psi|, sign) of a configuration by the boundary-MPS contraction closed at row
+    Ly // 2 (the amplitude the measurement reports)."""
+    Ly = len(grid)
+    k = Ly // 2
+    Ts, logT = vmc.top_envs(grid, spins, chi, W, n_fit, upto=k)
+    Bs, logB = vmc.bottom_envs(grid, spins, chi, W, n_fit)
+    return vmc.row_psi(Ts[k], vmc.row_tensors(grid, spins, k), Bs[k], logT[k], logB[k])
+
+
+def random_attempt(grid, spins, chi, W, n_fit, seed, chain, sweep, attempt, cur=None, record=None):
+    """One attempt of the random-NNASP scheme (Eq. (prob_r)) from configuration `spins`
+    with the Philox uniforms of (chain, sweep, attempt); see attempt_with."""
+    word, r = philox.random_attempt_words(seed, chain, sweep, attempt)
+    return attempt_with(grid, spins, chi, W, n_fit, word, r, cur, record)
+
+
+def attempt_with(grid, spins, chi, W, n_fit, word, r, cur=None, record=None, force=None):
+    """The attempt for a given pick word and acceptance uniform r: the K_a antiparallel
+    NN pairs of S_a are listed in the sweep's bond order, the pair with index
+    pick(word, K_a) is swapped, and the trial S_b is accepted when
+    r < min[1, (|Psi(S_b)|^2 / K_b) / (|Psi(S_a)|^2 / K_a)].  `cur` = (ln|Psi|, sign) of
+    `spins` (computed when None).  Returns (new spins, (ln|Psi|, sign) of them); `record`
+    (list) receives (bond id, ratio Psi(S_b)/Psi(S_a), K_a, K_b, decision).  `force`
+    (True / False) replaces the decision (replaying another implementation's decision at
+    a near-tie)."""
+    spins = np.asarray(spins)
+    Ly, Lx = spins.shape
+    flat = spins.ravel()
+    bonds = nn_bonds(Ly, Lx)
+    if cur is None:
+        cur = boundary_psi(grid, spins, chi, W, n_fit)
+    pairs = [(n, i, j) for n, (i, j) in enumerate(bonds) if flat[i] != flat[j]]
+    if not pairs:
+        if record is not None:
+            record.append((-1, 0.0, 0, 0, False))
+        return spins.copy(), cur
+    bond, i, j = pairs[philox.pick(word, len(pairs))]
+    trial = _swap(flat, i, j).reshape(Ly, Lx)
+    new = boundary_psi(grid, trial, chi, W, n_fit)
+    Ka = len(pairs)
+    Kb = len(nnasps(trial.ravel(), bonds))
+    rho = new[1] * cur[1] * np.exp(new[0] - cur[0])
+    accept = r < min(1.0, rho * rho * Ka / Kb) if force is None else bool(force)
+    if record is not None:
+        record.append((bond, rho, Ka, Kb, bool(accept)))
+    return (trial, new) if accept else (spins.copy(), cur)
+
+
+def random_sweep(grid, spins, chi, W, n_fit, seed, chain, sweep, record=None):
+    """One sweep of the random scheme: N = Ly Lx attempts (Sec. II A)."""
+    spins = np.asarray(spins).copy()
+    cur = boundary_psi(grid, spins, chi, W, n_fit)
+    for t in range(spins.size):
+        spins, cur = random_attempt(grid, spins, chi, W, n_fit, seed, chain, sweep, t, cur, record)
+    return spins

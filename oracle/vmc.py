@@ -16,7 +16,7 @@ Conventions
   Bottom environment B_k covers rows > k; its physical legs are the d legs of row k.
   (App. B: |U_k> = M_k |U_{k-1}>, <D_k| = <D_{k+1}| M_k.)
 
-Readings of points the paper leaves open (each is listed in the design notes):
+Readings of points the paper leaves open:
 * Truncation (App. B): the variational fit min ||M|U> - |U'>||^2 by one-site
   sweeps.  Its initial guess is a fixed random MPS (the ``sketch``, an input) brought
   to right-orthonormal form site by site; the first left-to-right sweep is then a

@@ -33,7 +33,8 @@ SYMBOLS = [
     "pepsvmc_set_graphs", "pepsvmc_set_proposal_params", "pepsvmc_get_proposal_params",
     "pepsvmc_proposal_logits", "pepsvmc_proposal_collect", "pepsvmc_proposal_dataset_size", "pepsvmc_proposal_load",
     "pepsvmc_proposal_train", "pepsvmc_train_proposal", "pepsvmc_set_proposal", "pepsvmc_learned_sweep", "pepsvmc_get_learned_trace",
-    "pepsvmc_env4_left", "pepsvmc_set_fused", "pepsvmc_set_wait_budget", "pepsvmc_get_sums", "pepsvmc_set_sums", "pepsvmc_sums_device", "pepsvmc_finalize_sums",
+    "pepsvmc_env4_left", "pepsvmc_set_fused", "pepsvmc_random_sweep", "pepsvmc_get_random_trace", "pepsvmc_set_wait_budget", "pepsvmc_get_sums", "pepsvmc_set_sums", "pepsvmc_sums_device", "pepsvmc_finalize_sums",
+    "pepsvmc_get_phi",
 ]
 
 
@@ -42,7 +43,7 @@ class Config(C.Structure):
                 ("n_chains", C.c_int32), ("n_fit", C.c_int32), ("J1", C.c_double),
                 ("J2", C.c_double), ("seed", C.c_uint64), ("precision", C.c_int32),
                 ("chi_measure", C.c_int32), ("wait_budget_cycles", C.c_uint64), ("chain_offset", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("symmetrize", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class PepsvmcError(RuntimeError):
@@ -109,11 +110,14 @@ def load(path: str | None = None):
         "pepsvmc_get_tuning": (C.c_int, [P, C.c_char_p, I64]),
         "pepsvmc_set_wait_budget": (C.c_int, [P, U64]),
         "pepsvmc_set_fused": (C.c_int, [P, I32]),
-        "pepsvmc_env4_left": (C.c_int, [P] + [P] * 8 + [I32] * 12),
+        "pepsvmc_random_sweep": (C.c_int, [P, I32, D]),
+        "pepsvmc_get_random_trace": (C.c_int, [P, C.POINTER(C.c_int32), D, I8]),
+        "pepsvmc_env4_left": (C.c_int, [P] + [P] * 8 + [I32] * 13),
         "pepsvmc_get_sums": (C.c_int, [P, D, D, D]),
         "pepsvmc_set_sums": (C.c_int, [P, D, D, D]),
         "pepsvmc_sums_device": (C.c_int, [P, C.POINTER(P), C.POINTER(P), C.POINTER(P)]),
         "pepsvmc_finalize_sums": (C.c_int, [P]),
+        "pepsvmc_get_phi": (C.c_int, [P, D, D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -10,7 +10,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import FP32, MIXED_BF16, MIXED_BF16X3, MIXED_TF32, PepsvmcError  # noqa: F401
+from ._lib import EINVAL, ESTATE, FP32, MIXED_BF16, MIXED_BF16X3, MIXED_TF32, PepsvmcError  # noqa: F401
 
 
 def _dp(a):
@@ -32,7 +32,8 @@ class PepsVMC:
     """
 
     def __init__(self, Ly, Lx, D, chi, n_chains, tensors, sketch, J1=1.0, J2=0.0, seed=0, n_fit=3,
-                 precision=FP32, stream=None, chi_measure=0, wait_budget_cycles=0, chain_offset=0):
+                 precision=FP32, stream=None, chi_measure=0, wait_budget_cycles=0, chain_offset=0,
+                 symmetrize=False):
         self.lib = _lib.load()
         cfg = _lib.Config()
         cfg.Ly, cfg.Lx, cfg.D, cfg.chi, cfg.n_chains, cfg.n_fit = Ly, Lx, D, chi, n_chains, n_fit
@@ -40,6 +41,7 @@ class PepsVMC:
         cfg.chi_measure = int(chi_measure)
         cfg.wait_budget_cycles = int(wait_budget_cycles)
         cfg.chain_offset = int(chain_offset)
+        cfg.symmetrize = 1 if symmetrize else 0
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -126,6 +128,21 @@ class PepsVMC:
         self._check(self.lib.pepsvmc_sample_sweep(self.ctx, int(n_sweeps), C.byref(r)))
         return r.value
 
+    def random_sweep(self, n_sweeps=1):
+        """Sweeps of the random-NNASP scheme (N attempts each); returns the acceptance rate."""
+        r = C.c_double()
+        self._check(self.lib.pepsvmc_random_sweep(self.ctx, int(n_sweeps), C.byref(r)))
+        return r.value
+
+    def get_random_trace(self):
+        shp = (self.n_chains, self.Ly * self.Lx)
+        bond = np.empty(shp, dtype=np.int32)
+        ratio = np.empty(shp)
+        dec = np.empty(shp, dtype=np.int8)
+        self._check(self.lib.pepsvmc_get_random_trace(self.ctx, bond.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                      _dp(ratio), _i8(dec)))
+        return bond, ratio, dec
+
     def enable_trace(self, on=True):
         self._check(self.lib.pepsvmc_enable_trace(self.ctx, 1 if on else 0))
 
@@ -141,6 +158,13 @@ class PepsVMC:
         sg = np.empty(self.n_chains, dtype=np.int8)
         self._check(self.lib.pepsvmc_measure(self.ctx, _dp(e), _dp(lp), _i8(sg)))
         return e, lp, sg
+
+    def phi(self):
+        """(E^Phi, w) per S, S-bar pair of the last measurement (symmetrize=True)."""
+        e = np.empty(self.n_chains // 2)
+        w = np.empty(self.n_chains // 2)
+        self._check(self.lib.pepsvmc_get_phi(self.ctx, _dp(e), _dp(w)))
+        return e, w
 
     def chain_grad(self, chain):
         g = np.empty(self.n_grad_entries)
@@ -180,12 +204,12 @@ class PepsVMC:
         self._check(self.lib.pepsvmc_env3_left(self.ctx, ptr(E), ptr(T), ptr(A), ptr(spins), ptr(B), ptr(out),
                                                *[int(v) for v in dims]))
 
-    def env4_left(self, E, T, A1, spins1, A2, spins2, B, out, dims):
+    def env4_left(self, E, T, A1, spins1, A2, spins2, B, out, dims, bmajor=False):
         """Four-line environment step on device tensors; ``dims`` = (n_chains, cT, cB, cT2,
-        cB2, D1l, D1r, Du1, Dd1, D2l, D2r, Dd2)."""
+        cB2, D1l, D1r, Du1, Dd1, D2l, D2r, Dd2); bmajor: E and out stored [b][a][l1][l2]."""
         ptr = lambda t: C.c_void_p(t if isinstance(t, int) else (t.data_ptr() if t is not None else 0))  # noqa: E731
         self._check(self.lib.pepsvmc_env4_left(self.ctx, ptr(E), ptr(T), ptr(A1), ptr(spins1), ptr(A2), ptr(spins2),
-                                               ptr(B), ptr(out), *[int(v) for v in dims]))
+                                               ptr(B), ptr(out), *[int(v) for v in dims], 1 if bmajor else 0))
 
     def get_profile_shapes(self):
         import json

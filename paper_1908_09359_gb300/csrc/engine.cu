@@ -690,7 +690,7 @@ struct pepsvmc_ctx {
       return fused3(fused_left(E, bsE, cT, cB, T, bsT, cT2, a, flip, B, bsB, cB2, out, bsO));
     GemmDesc g[3];
     env3_left_descs(g, Env3Dims{cT, cB, cT2, cB2, a.Dl, a.Dr, a.Du, a.Dd}, E, bsE, T, bsT, a.lurd, a.size,
-                    spins + a.spin, (long long)Ly * Lx, flip, B, bsB, out, bsO, tmp1, tmp2, SI);
+                    (sel_base ? sel_base : spins) + a.spin, (long long)Ly * Lx, flip, B, bsB, out, bsO, tmp1, tmp2, SI);
     for (int i = 0; i < 3; ++i) PV_CUDA(gemm(g[i]));
     return cudaSuccess;
   }
@@ -707,15 +707,15 @@ struct pepsvmc_ctx {
       PV_CUDA(fused3(fused_left(E, bsE, cT, cB, T, bsT, cT2, a, 0, B, bsB, cB2, out0, bsO)));
       if (out1) PV_CUDA(fused3(fused_left(E, bsE, cT, cB, T, bsT, cT2, a, 1, B, bsB, cB2, out1, bsO)));
       if (!keep_et) return cudaSuccess;
-      env3_left_descs(g, d, E, bsE, T, bsT, a.lurd, a.size, spins + a.spin, (long long)Ly * Lx, 0, B, bsB, out0,
+      env3_left_descs(g, d, E, bsE, T, bsT, a.lurd, a.size, (sel_base ? sel_base : spins) + a.spin, (long long)Ly * Lx, 0, B, bsB, out0,
                       bsO, tmp1, tmp2, SI);
       return gemm(g[0]);
     }
-    env3_left_descs(g, d, E, bsE, T, bsT, a.lurd, a.size, spins + a.spin, (long long)Ly * Lx, 0, B, bsB, out0, bsO,
+    env3_left_descs(g, d, E, bsE, T, bsT, a.lurd, a.size, (sel_base ? sel_base : spins) + a.spin, (long long)Ly * Lx, 0, B, bsB, out0, bsO,
                     tmp1, tmp2, SI);
     for (int i = 0; i < 3; ++i) PV_CUDA(gemm(g[i]));
     if (!out1) return cudaSuccess;
-    env3_left_descs(g, d, E, bsE, T, bsT, a.lurd, a.size, spins + a.spin, (long long)Ly * Lx, 1, B, bsB, out1, bsO,
+    env3_left_descs(g, d, E, bsE, T, bsT, a.lurd, a.size, (sel_base ? sel_base : spins) + a.spin, (long long)Ly * Lx, 1, B, bsB, out1, bsO,
                     tmp1, tmp2, SI);
     PV_CUDA(gemm(g[1]));
     return gemm(g[2]);
@@ -1098,6 +1098,47 @@ struct pepsvmc_ctx {
     return cudaSuccess;
   }
 
+  // ------------------------ spin-inversion symmetrised sampling (end of Sec. II B)
+  // Chains p and p + pairs hold S and S-bar.  At the start of each phase w of every
+  // chain is taken afresh from the two amplitudes closed at row 0 of the phase's lattice
+  // (trivial top, the phase's bottom environment of row 0 at the sampler's cutoff), then
+  // carried through the phase by k_phi_decide.
+  bool sym = false;
+  int pairs = 0;
+  double *phi_rho = nullptr, *phi_w = nullptr, *phi_wm = nullptr, *eloc_phi = nullptr, *phi_wt = nullptr;
+  double* phi_lp = nullptr;
+  int8_t* phi_sg = nullptr;
+  int* phi_exps = nullptr;
+  cudaError_t phase_weight(int o, Store& top, Store& bot) {
+    const Orient& Ob = O[o];
+    const View T = view(top, 0, 0);
+    const View B = view(bot, Ob.Ly - 1, Ob.Ly - 1);
+    const std::vector<int>& tb = *T.bond;
+    const std::vector<int>& bb = *B.bond;
+    PV_CUDA(ms(phi_exps, 0, C * sizeof(int)));
+    const float* Lin = ones;
+    long long bsL = 1;
+    for (int m = 0; m < Ob.Lx; ++m) {
+      const SiteOp a = site(o, 0, m);
+      float* cur = l3[(m + 1) % 2];
+      PV_CUDA(left3(Lin, bsL, tb[m], bb[m], T.site(m), T.chain_stride, tb[m + 1], a, 0, B.site(m),
+                    B.chain_stride, bb[m + 1], cur, S));
+      if (m + 1 < Ob.Lx) {
+        PV_CUDA(norm2(cur, S, tb[m + 1] * a.Dr * bb[m + 1], nullptr, 0, nullptr, 0, phi_exps));
+      } else {
+        if (!chains(cur, S, 1, 4, "phase amplitude") || !chains(T.logs, 1, 1, 8, "logT") ||
+            !chains(B.logs, 1, 1, 8, "logB"))
+          return cudaErrorInvalidValue;
+        launches += 2;
+        PV_CUDA(k_logpsi(cur, S, phi_exps, T.logs, B.logs, phi_lp, phi_sg, C, status, st));
+        PV_CUDA(k_phi_combine(phi_lp, phi_sg, nullptr, C, pairs, phi_w, nullptr, nullptr, status, st));
+      }
+      Lin = cur;
+      bsL = S;
+    }
+    return cudaSuccess;
+  }
+
   // --------------------------------------------- sequential sweep (Sec. II A, Eq. (9))
   // Horizontal bonds of every row of orientation o.  `top` receives T_k (slot = row, or
   // row % 2 when `pingpong`), `bot` must hold the top environments of the upside-down
@@ -1108,6 +1149,7 @@ struct pepsvmc_ctx {
     auto slot_of = [&](int row) { return pingpong ? (row % 2) : row; };
     auto envRp = [&](int m) { return envR + (long long)m * C * S; };
     auto envRfp = [&](int m) { return envRf + (long long)m * C * S; };
+    if (sym) PV_CUDA(phase_weight(o, top, bot));
     for (int k = 0; k < Lyo; ++k) {
       const View T = view(top, k, slot_of(k));
       const int kb = Lyo - 1 - k;
@@ -1151,8 +1193,17 @@ struct pepsvmc_ctx {
             !chains(spins, ma.spin_stride, std::max(ma.site_a, ma.site_b) + 1, 1, "metropolis spins") ||
             (ma.trace_ratio && !chains(ma.trace_ratio, nbonds(), ma.bond + 1, 8, "trace")))
           return cudaErrorInvalidValue;
-        ++launches;
-        PV_CUDA(k_metropolis(ma, C, st));
+        if (sym) {
+          ma.rho_out = phi_rho;
+          ma.phi_w = phi_w;
+          ma.pairs = pairs;
+          launches += 2;
+          PV_CUDA(k_metropolis(ma, C, st));
+          PV_CUDA(k_phi_decide(ma, C, st));
+        } else {
+          ++launches;
+          PV_CUDA(k_metropolis(ma, C, st));
+        }
         Lin = l3[0];
         bsL = S;
       }
@@ -1195,9 +1246,10 @@ struct pepsvmc_ctx {
     if (proposal_mode == 1) PV_CUDA(learned_sweep());
     PV_CUDA(measure_dev());
     launches += 2;
-    PV_CUDA(k_energy_accum(eloc, C, sums, st));
+    // symmetrised: one sample per pair, E^Phi for both chains, G weighted into G^Phi
+    PV_CUDA(k_energy_accum(sym ? eloc_phi : eloc, sym ? pairs : C, sums, st));
     return k_grad_accum(G, Ph, Ph, elem_site, d_site_half_off, d_site_full_off, d_site_size, d_site_spin, spins,
-                        (long long)Ly * Lx, eloc, C, sumG, sumGE, st);
+                        (long long)Ly * Lx, sym ? eloc_phi : eloc, C, sumG, sumGE, st, sym ? phi_wt : nullptr);
   }
   void drop_graph() {
     if (step_exec) cudaGraphExecDestroy(step_exec);
@@ -1254,9 +1306,13 @@ struct pepsvmc_ctx {
       top_valid = false;
       const cudaError_t e = measure_at_cutoff();
       chi = chi_s;
-      return e;
+      PV_CUDA(e);
+    } else {
+      PV_CUDA(measure_at_cutoff());
     }
-    return measure_at_cutoff();
+    if (!sym) return cudaSuccess;
+    ++launches;
+    return k_phi_combine(logpsi, sign, eloc, C, pairs, phi_wm, eloc_phi, phi_wt, status, st);
   }
   cudaError_t measure_at_cutoff() {
     if (!top_valid) {
@@ -1551,6 +1607,56 @@ struct pepsvmc_ctx {
     return cudaSuccess;
   }
 
+  // ------------------------------------------ random-NNASP sweep (Sec. II A, Eq. (prob_r))
+  // N attempts; each proposes one uniformly chosen antiparallel NN pair per chain and
+  // needs Psi of every chain's trial configuration: a full boundary-MPS contraction
+  // (closed at row Ly/2, as the measurement's amplitude) with the site tensors selected
+  // by the trial spins.  Psi of the current configurations is kept across attempts.
+  int8_t *r_prop = nullptr, *r_sg = nullptr, *r_tr_dec = nullptr;
+  int *r_Ka = nullptr, *r_Kb = nullptr, *r_bond = nullptr, *r_tr_bond = nullptr;
+  double *r_lp = nullptr, *r_tr_ratio = nullptr;
+  cudaError_t random_alloc() {
+    if (r_prop) return cudaSuccess;
+    const long long N = (long long)Ly * Lx;
+    PV_CUDA(alloc(&r_prop, C * N));
+    PV_CUDA(alloc(&r_sg, C));
+    PV_CUDA(alloc(&r_Ka, C));
+    PV_CUDA(alloc(&r_Kb, C));
+    PV_CUDA(alloc(&r_bond, C));
+    PV_CUDA(alloc(&r_lp, C));
+    PV_CUDA(alloc(&r_tr_bond, C * N));
+    PV_CUDA(alloc(&r_tr_ratio, C * N));
+    PV_CUDA(alloc(&r_tr_dec, C * N));
+    return cudaSuccess;
+  }
+  cudaError_t random_sweep() {
+    PV_CUDA(random_alloc());
+    const int kstar = Ly / 2;
+    const long long N = (long long)Ly * Lx;
+    PV_CUDA(amplitude_dev(kstar));
+    PV_CUDA(cp(r_lp, logpsi, C * sizeof(double), cudaMemcpyDeviceToDevice));
+    PV_CUDA(cp(r_sg, sign, C, cudaMemcpyDeviceToDevice));
+    RandomArgs ra{};
+    ra.spins = spins; ra.prop = r_prop; ra.C = C; ra.Ly = Ly; ra.Lx = Lx;
+    ra.key = cfg.seed; ra.sweep = d_sweep; ra.chain_base = chain_base;
+    ra.Ka = r_Ka; ra.Kb = r_Kb; ra.bond = r_bond;
+    ra.lp_cur = r_lp; ra.sg_cur = r_sg; ra.lp_new = logpsi; ra.sg_new = sign;
+    ra.tr_bond = trace_on ? r_tr_bond : nullptr; ra.tr_ratio = r_tr_ratio; ra.tr_dec = r_tr_dec; ra.tr_stride = N;
+    ra.counters = counters; ra.status = status;
+    for (int t = 0; t < N; ++t) {
+      ra.attempt = t;
+      launches += 2;
+      PV_CUDA(k_random_propose(ra, st));
+      sel_base = r_prop;
+      const cudaError_t e = amplitude_dev(kstar);
+      sel_base = nullptr;
+      PV_CUDA(e);
+      PV_CUDA(k_random_accept(ra, st));
+    }
+    top_valid = false;
+    return cudaSuccess;
+  }
+
   cudaError_t refresh_perms() {
     for (int o = 0; o < 4; ++o)
       for (int t = 0; t < 2; ++t) {
@@ -1610,7 +1716,9 @@ int validate(const pepsvmc_config* c, std::string& why) {
   }
   if (c->chain_offset < 0) { why = "chain_offset must be >= 0"; return PEPSVMC_EINVAL; }
   if (c->wait_budget_cycles > (uint64_t)1 << 62) { why = "wait_budget_cycles too large"; return PEPSVMC_EINVAL; }
-  for (int i = 0; i < 3; ++i)
+  if (c->symmetrize != 0 && c->symmetrize != 1) { why = "symmetrize must be 0 or 1"; return PEPSVMC_EINVAL; }
+  if (c->symmetrize && c->n_chains % 2) { why = "symmetrize needs an even n_chains (S, S-bar pairs)"; return PEPSVMC_EINVAL; }
+  for (int i = 0; i < 2; ++i)
     if (c->reserved[i]) { why = "reserved fields must be zero"; return PEPSVMC_EINVAL; }
   return PEPSVMC_OK;
 }
@@ -1736,6 +1844,16 @@ int setup(pepsvmc_ctx* x, const double* tensors, const double* sketch) {
   ALLOC(x->status, 1);
   ALLOC(x->counters, 2);
   ALLOC(x->d_sweep, 1);
+  if (x->sym) {
+    ALLOC(x->phi_rho, C);
+    ALLOC(x->phi_w, C);
+    ALLOC(x->phi_wm, C);
+    ALLOC(x->eloc_phi, C);
+    ALLOC(x->phi_wt, C);
+    ALLOC(x->phi_lp, C);
+    ALLOC(x->phi_sg, C);
+    ALLOC(x->phi_exps, C);
+  }
   // site tables for the gradient accumulation
   {
     std::vector<int> es(x->Ph), sp(Ly * Lx);
@@ -1769,7 +1887,8 @@ int setup(pepsvmc_ctx* x, const double* tensors, const double* sketch) {
   std::vector<int8_t> neel((size_t)C * Ly * Lx);
   for (int c = 0; c < C; ++c)
     for (int k = 0; k < Ly; ++k)
-      for (int m = 0; m < Lx; ++m) neel[((size_t)c * Ly + k) * Lx + m] = ((k + m) % 2 == 0) ? 1 : -1;
+      for (int m = 0; m < Lx; ++m)
+        neel[((size_t)c * Ly + k) * Lx + m] = (((k + m) % 2 == 0) != (x->sym && c >= x->pairs)) ? 1 : -1;
   if ((e = x->cps(x->spins, neel.data(), neel.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return x->fail_cuda(e);
   if ((e = x->sync()) != cudaSuccess) return x->fail_cuda(e);
   return PEPSVMC_OK;
@@ -1810,6 +1929,8 @@ int pepsvmc_init(const pepsvmc_config* cfg, const double* tensors, const double*
   x->nfit = cfg->n_fit;
   x->wait_budget = (long long)cfg->wait_budget_cycles;
   x->chain_base = (unsigned)cfg->chain_offset;
+  x->sym = cfg->symmetrize != 0;
+  x->pairs = x->sym ? x->C / 2 : 0;
   return setup(x, tensors, sketch);
 }
 
@@ -1871,8 +1992,9 @@ int pepsvmc_env3_left(pepsvmc_ctx* x, const float* E, const float* T, const floa
 int pepsvmc_env4_left(pepsvmc_ctx* x, const float* E, const float* T, const float* A1, const int8_t* spins1,
                       const float* A2, const int8_t* spins2, const float* B, float* out, int32_t n_chains, int32_t cT,
                       int32_t cB, int32_t cT2, int32_t cB2, int32_t D1l, int32_t D1r, int32_t Du1, int32_t Dd1,
-                      int32_t D2l, int32_t D2r, int32_t Dd2) {
+                      int32_t D2l, int32_t D2r, int32_t Dd2, int32_t bmajor) {
   if (!x) return PEPSVMC_EINVAL;
+  if (bmajor != 0 && bmajor != 1) return x->fail(PEPSVMC_EINVAL, "env4_left: bmajor must be 0 or 1");
   const int dims[11] = {cT, cB, cT2, cB2, D1l, D1r, Du1, Dd1, D2l, D2r, Dd2};
   if (!E || !T || !A1 || !A2 || !B || !out || n_chains < 1)
     return x->fail(PEPSVMC_EINVAL, "env4_left: null pointer or no chains");
@@ -1889,19 +2011,28 @@ int pepsvmc_env4_left(pepsvmc_ctx* x, const float* E, const float* T, const floa
   if (x->fused4_ok(f)) {
     f.batch = n_chains;
     f.wait_cycles = x->wait_budget;
-    f.E = E; f.bsE = (long long)cT * D1l * D2l * cB; f.sEa = (long long)D1l * D2l * cB; f.sEl1 = (long long)D2l * cB;
-    f.sEl2 = cB; f.sEb = 1;
+    f.E = E; f.bsE = (long long)cT * D1l * D2l * cB;
+    if (bmajor) {
+      f.sEb = (long long)cT * D1l * D2l; f.sEa = (long long)D1l * D2l; f.sEl1 = D2l; f.sEl2 = 1;
+    } else {
+      f.sEa = (long long)D1l * D2l * cB; f.sEl1 = (long long)D2l * cB; f.sEl2 = cB; f.sEb = 1;
+    }
     f.T = T; f.bsT = (long long)cT * Du1 * cT2; f.sTa = (long long)Du1 * cT2; f.sTu = cT2; f.sTa2 = 1;
     f.A1 = A1; f.ss1 = s1; f.s1l = (long long)Du1 * D1r * Dd1; f.s1u = (long long)D1r * Dd1; f.s1r = Dd1; f.s1d = 1;
     f.A2 = A2; f.ss2 = s2; f.s2l = (long long)Dd1 * D2r * Dd2; f.s2u = (long long)D2r * Dd2; f.s2r = Dd2; f.s2d = 1;
     f.sel1 = spins1; f.sel2 = spins2; f.sel_stride = 1;
     f.B = B; f.bsB = (long long)cB * Dd2 * cB2; f.sBb = (long long)Dd2 * cB2; f.sBd = cB2; f.sBb2 = 1;
-    f.out = out; f.bsO = (long long)cT2 * D1r * D2r * cB2; f.sOa2 = (long long)D1r * D2r * cB2;
-    f.sOr1 = (long long)D2r * cB2; f.sOr2 = cB2; f.sOb2 = 1;
+    f.out = out; f.bsO = (long long)cT2 * D1r * D2r * cB2;
+    if (bmajor) {
+      f.sOb2 = (long long)cT2 * D1r * D2r; f.sOa2 = (long long)D1r * D2r; f.sOr1 = D2r; f.sOr2 = 1;
+    } else {
+      f.sOa2 = (long long)D1r * D2r * cB2; f.sOr1 = (long long)D2r * cB2; f.sOr2 = cB2; f.sOb2 = 1;
+    }
     ++x->launches;
     cudaError_t e = env4_fused(f, x->tc_mode() == 3, x->status, x->st);
     return e == cudaSuccess ? PEPSVMC_OK : x->fail_cuda(e);
   }
+  if (bmajor) return x->fail(PEPSVMC_EINVAL, "env4_left: the b-major layout needs the fused kernel");
   // four separate products, as left4_x / left4_y / left4_zw with the caller's spins
   GemmDesc g[4];
   float* t1 = x->tmp1;
@@ -2109,6 +2240,7 @@ int pepsvmc_proposal_train(pepsvmc_ctx* x, int32_t epochs, int32_t batch, double
 
 int pepsvmc_set_proposal(pepsvmc_ctx* x, int32_t mode) {
   if (!x || mode < 0 || mode > 1) return PEPSVMC_EINVAL;
+  if (mode == 1 && x->sym) return x->fail(PEPSVMC_EINVAL, "symmetrize: only the sequential sweep samples |Phi|^2");
   if (mode == 1 && !x->net_ready) return x->fail(PEPSVMC_ESTATE, "no proposal network: call pepsvmc_set_proposal_params");
   x->proposal_mode = mode;
   x->drop_graph();
@@ -2118,6 +2250,7 @@ int pepsvmc_set_proposal(pepsvmc_ctx* x, int32_t mode) {
 
 int pepsvmc_learned_sweep(pepsvmc_ctx* x, int32_t n, double* rate) {
   if (!x || n < 0) return PEPSVMC_EINVAL;
+  if (x->sym) return x->fail(PEPSVMC_EINVAL, "symmetrize: only the sequential sweep samples |Phi|^2");
   if (!x->net_ready) return x->fail(PEPSVMC_ESTATE, "no proposal network: call pepsvmc_set_proposal_params");
   cudaError_t e = x->ms(x->lcount, 0, 2 * sizeof(unsigned long long));
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
@@ -2211,6 +2344,12 @@ int pepsvmc_set_spins(pepsvmc_ctx* x, const int8_t* s) {
   const size_t n = (size_t)x->C * x->Ly * x->Lx;
   for (size_t i = 0; i < n; ++i)
     if (s[i] != 1 && s[i] != -1) return x->fail(PEPSVMC_EINVAL, "spins must be +1 or -1");
+  if (x->sym) {
+    const size_t half = n / 2;
+    for (size_t i = 0; i < half; ++i)
+      if (s[half + i] != -s[i])
+        return x->fail(PEPSVMC_EINVAL, "symmetrize: chain p + n_chains/2 must be the inversion of chain p");
+  }
   cudaError_t e = x->cp(x->spins, s, n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = x->sync();
   if (e != cudaSuccess) return x->fail_cuda(e);
@@ -2304,6 +2443,17 @@ int pepsvmc_measure(pepsvmc_ctx* x, double* eloc, double* logpsi, int8_t* sign) 
   return PEPSVMC_OK;
 }
 
+int pepsvmc_get_phi(pepsvmc_ctx* x, double* eloc_phi, double* w) {
+  if (!x) return PEPSVMC_EINVAL;
+  if (!x->sym) return x->fail(PEPSVMC_ESTATE, "get_phi: the context was created without symmetrize");
+  if (!x->have_measure) return x->fail(PEPSVMC_ESTATE, "no measurement yet");
+  cudaError_t e = cudaSuccess;
+  if (eloc_phi) e = x->cp(eloc_phi, x->eloc_phi, x->pairs * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && w) e = x->cp(w, x->phi_wm, x->pairs * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = x->sync();
+  return e == cudaSuccess ? PEPSVMC_OK : x->fail_cuda(e);
+}
+
 int pepsvmc_get_chain_grad(pepsvmc_ctx* x, int32_t chain, double* out) {
   if (!x || !out || chain < 0 || chain >= x->C) return PEPSVMC_EINVAL;
   if (!x->have_measure) return x->fail(PEPSVMC_ESTATE, "no measurement yet");
@@ -2339,7 +2489,8 @@ int pepsvmc_energy_and_grad(pepsvmc_ctx* x, int32_t n, double* E_mean, double* E
     ++x->sweep_counter;
     x->top_valid = true;
     x->have_measure = true;
-    if (eloc && (e = x->cp(eloc + (size_t)t * x->C, x->eloc, x->C * sizeof(double), cudaMemcpyDeviceToHost)))
+    if (eloc && (e = x->cp(eloc + (size_t)t * x->C, x->sym ? x->eloc_phi : x->eloc, x->C * sizeof(double),
+                           cudaMemcpyDeviceToHost)))
       return x->fail_cuda(e);
     if (logpsi && (e = x->cp(logpsi + (size_t)t * x->C, x->logpsi, x->C * sizeof(double), cudaMemcpyDeviceToHost)))
       return x->fail_cuda(e);
@@ -2358,6 +2509,39 @@ int pepsvmc_energy_and_grad(pepsvmc_ctx* x, int32_t n, double* E_mean, double* E
   if (E_var) *E_var = s[1] / s[2] - mean * mean;
   if (grad && (e = x->cps(grad, x->grad, x->P * sizeof(double), cudaMemcpyDeviceToHost))) return x->fail_cuda(e);
   return PEPSVMC_OK;
+}
+
+int pepsvmc_random_sweep(pepsvmc_ctx* x, int32_t n, double* rate) {
+  if (!x || n < 0) return PEPSVMC_EINVAL;
+  if (x->sym) return x->fail(PEPSVMC_EINVAL, "symmetrize: only the sequential sweep samples |Phi|^2");
+  cudaError_t e = x->ms(x->counters, 0, 2 * sizeof(unsigned long long));
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    e = x->set_sweep();
+    if (e == cudaSuccess) e = x->random_sweep();
+    ++x->sweep_counter;
+  }
+  if (e != cudaSuccess) return x->fail_cuda(e);
+  int rc = x->check_status();
+  if (rc) return rc;
+  if (rate) {
+    unsigned long long h[2];
+    e = x->cps(h, x->counters, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return x->fail_cuda(e);
+    *rate = h[0] ? (double)h[1] / (double)h[0] : 0.0;
+  }
+  return PEPSVMC_OK;
+}
+
+int pepsvmc_get_random_trace(pepsvmc_ctx* x, int32_t* bond, double* ratio, int8_t* decision) {
+  if (!x) return PEPSVMC_EINVAL;
+  if (!x->r_tr_bond || !x->trace_on) return x->fail(PEPSVMC_ESTATE, "no traced random sweep");
+  const size_t n = (size_t)x->C * x->Ly * x->Lx;
+  cudaError_t e = cudaSuccess;
+  if (bond) e = x->cp(bond, x->r_tr_bond, n * sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && ratio) e = x->cp(ratio, x->r_tr_ratio, n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && decision) e = x->cp(decision, x->r_tr_dec, n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = x->sync();
+  return e == cudaSuccess ? PEPSVMC_OK : x->fail_cuda(e);
 }
 
 int pepsvmc_set_fused(pepsvmc_ctx* x, int32_t on) {

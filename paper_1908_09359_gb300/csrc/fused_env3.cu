@@ -75,28 +75,41 @@ struct Unit {
 };
 __device__ __forceinline__ Unit unit_of(int u, int n_at) { return Unit{u / n_at, u % n_at}; }
 
-// One b tile's operands in registers: the E slice (rows b*8 + l, K = a; two units of 8
-// per thread) and the B slice (rows b', K = b*8 + d; two units of 8 per thread).
+// One b tile's operands in registers: the E slice (rows b*8 + l, K = a: the two rows of
+// a pair of consecutive b at one l, one K chunk of 8) and the B slice (rows b', K = b*8 + d;
+// two units of 8 per thread).
 struct Slice {
   float e[2][8];
   float b[2][8];
 };
 
+// E slice lanes: l fastest, then the b pair, then the K chunk.  The eight lanes of one
+// shared-memory store phase then write rows of eight different l, i.e. eight different
+// 16-byte bank groups of the K-major tile, and the global reads of one K value cover
+// eight runs of eight consecutive b (full 32-byte sectors when b is contiguous).
 __device__ __forceinline__ void fetch_slice(const Env3Fused& a, int c, int j, int tid, Slice& s) {
   const float* E = a.E + (long long)c * a.bsE;
   const float* B = a.B + (long long)c * a.bsB;
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    // lanes run along b (contiguous in the usual storage), then l and the K chunk
-    const int u = tid + i * kThreads;
-    const int bl = u & 15, l = (u >> 4) & 7, kc = u >> 7;
-    const int b = j * kBT + bl;
-    const bool rv = b < a.cB && l < a.Dl;
-    const float* src = E + b * a.sEb + l * a.sEl;
+  {
+    const int l = tid & 7, bp = (tid >> 3) & 7, kc = tid >> 6;
+    const int b0 = j * kBT + 2 * bp;
+    const bool lv = l < a.Dl;
+    const float* src = E + (long long)b0 * a.sEb + l * a.sEl;
+    // pairs of b as one 8-byte load when b is contiguous and every pair start is aligned
+    const bool vec = a.sEb == 1 && ((a.sEl | a.sEa | a.bsE) & 1) == 0 && (reinterpret_cast<uintptr_t>(a.E) & 7) == 0 &&
+                     b0 + 1 < a.cB;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int k = kc * 8 + e;
-      s.e[i][e] = (rv && k < a.cT) ? src[k * a.sEa] : 0.f;
+      const bool kv = lv && k < a.cT;
+      if (vec) {
+        float2 v = kv ? *reinterpret_cast<const float2*>(src + k * a.sEa) : make_float2(0.f, 0.f);
+        s.e[0][e] = v.x;
+        s.e[1][e] = v.y;
+      } else {
+        s.e[0][e] = (kv && b0 < a.cB) ? src[k * a.sEa] : 0.f;
+        s.e[1][e] = (kv && b0 + 1 < a.cB) ? src[k * a.sEa + a.sEb] : 0.f;
+      }
     }
   }
 #pragma unroll
@@ -112,12 +125,9 @@ __device__ __forceinline__ void fetch_slice(const Env3Fused& a, int c, int j, in
 
 template <bool X3>
 __device__ __forceinline__ void store_e(uint8_t* sm, int tid, const Slice& s) {
+  const int l = tid & 7, bp = (tid >> 3) & 7, kc = tid >> 6;
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int u = tid + i * kThreads;
-    const int row = (u & 15) * 8 + ((u >> 4) & 7);  // b*8 + l
-    put16<2, X3>(sm + OFF_E + kmajor_off(row, (u >> 7) * 8, 4), s.e[i], SZ_E);
-  }
+  for (int i = 0; i < 2; ++i) put16<2, X3>(sm + OFF_E + kmajor_off((2 * bp + i) * 8 + l, kc * 8, 4), s.e[i], SZ_E);
 }
 template <bool X3>
 __device__ __forceinline__ void store_b(uint8_t* sm, int buf, int tid, const Slice& s) {

@@ -123,6 +123,21 @@ __global__ void mps_normalize_kernel(float* x, long long bs, int n, const int* e
   }
 }
 
+// L(m) of the chosen configuration (src), scaled by a power of two to max |.| in [1/2, 1).
+__device__ void select_left(const MetropolisArgs& a, int b, const float* src, float* redf) {
+  float mx = 0.f;
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x) mx = fmaxf(mx, fabsf(src[i]));
+  mx = block_max(mx, redf);
+  float s = 1.f;
+  if (mx > 0.f && isfinite(mx)) {
+    int e;
+    frexpf(mx, &e);
+    s = ldexpf(1.f, -e);
+  }
+  float* out = a.out + b * a.bs_out;
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x) out[i] = src[i] * s;
+}
+
 // Sequential Metropolis step on one pair (Eq. (9)) for every chain.
 __global__ void metropolis_kernel(const MetropolisArgs a) {
   __shared__ double red[kThreads / 32];
@@ -141,6 +156,19 @@ __global__ void metropolis_kernel(const MetropolisArgs a) {
   if (anti) {
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) num += (double)fl[i] * Rf[i];
     num = block_sum(num, red);
+  }
+  if (a.rho_out) {  // symmetrised sampling: the ratio only, decided per pair
+    if (threadIdx.x == 0) {
+      double rho = 0.0;
+      if (den == 0.0) atomicOr(a.status, ST_ZEROPSI);
+      else if (anti) rho = num / den;
+      if (!isfinite(rho)) {
+        atomicOr(a.status, ST_NONFINITE);
+        rho = 0.0;
+      }
+      a.rho_out[b] = rho;
+    }
+    return;
   }
   if (threadIdx.x == 0) {
     int accept = 0;
@@ -175,18 +203,75 @@ __global__ void metropolis_kernel(const MetropolisArgs a) {
     acc_s = accept;
   }
   __syncthreads();
-  const float* src = acc_s ? fl : cur;
-  float mx = 0.f;
-  for (int i = threadIdx.x; i < a.n; i += blockDim.x) mx = fmaxf(mx, fabsf(src[i]));
-  mx = block_max(mx, redf);
-  float s = 1.f;
-  if (mx > 0.f && isfinite(mx)) {
-    int e;
-    frexpf(mx, &e);
-    s = ldexpf(1.f, -e);
+  select_left(a, b, acc_s ? fl : cur, redf);
+}
+
+// Symmetrised decision of pair p = b mod pairs, taken identically by the blocks of both
+// chains of the pair (each applies it to its own spins, L(m) and copy of w).
+__global__ void phi_decide_kernel(const MetropolisArgs a) {
+  __shared__ float redf[kThreads / 32];
+  __shared__ int acc_s;
+  const int b = blockIdx.x;
+  const int p = b % a.pairs;
+  int8_t* sp = a.spins + b * a.spin_stride;
+  if (threadIdx.x == 0) {
+    int accept = 0;
+    const double r1 = a.rho_out[p], r2 = a.rho_out[p + a.pairs];
+    const double w = a.phi_w[b];
+    if (sp[a.site_a] != sp[a.site_b]) {
+      const double num = r1 + w * r2, den = 1.0 + w;
+      if (den == 0.0) atomicOr(a.status, ST_ZEROPSI);
+      const double q = den != 0.0 ? (num / den) * (num / den) : 0.0;
+      if (!isfinite(q)) {
+        atomicOr(a.status, ST_NONFINITE);
+      } else if (den != 0.0) {
+        const uint4 u4 = philox4x32_10(
+            make_uint4((unsigned)p + a.chain_base, (unsigned)*a.sweep, (unsigned)a.bond, kTagMetropolis),
+            make_uint2((unsigned)(a.key & 0xffffffffull), (unsigned)(a.key >> 32)));
+        accept = (uniform24(u4.x) < fmin(1.0, q)) ? 1 : 0;
+      }
+      if (accept) {
+        if (r1 == 0.0) {  // Psi(S') = 0: w of the new configuration is undefined
+          atomicOr(a.status, ST_NONFINITE);
+        } else {
+          a.phi_w[b] = w * r2 / r1;
+        }
+        sp[a.site_a] = (int8_t)-sp[a.site_a];
+        sp[a.site_b] = (int8_t)-sp[a.site_b];
+      }
+      if (b < a.pairs) {
+        atomicAdd(&a.counters[0], 1ull);
+        if (accept) atomicAdd(&a.counters[1], 1ull);
+      }
+      if (a.trace_ratio) a.trace_ratio[b * a.trace_stride + a.bond] = b < a.pairs ? r1 : r2;
+      if (a.trace_dec) a.trace_dec[b * a.trace_stride + a.bond] = (int8_t)accept;
+    } else {
+      if (a.trace_ratio) a.trace_ratio[b * a.trace_stride + a.bond] = 0.0;
+      if (a.trace_dec) a.trace_dec[b * a.trace_stride + a.bond] = (int8_t)-1;
+    }
+    acc_s = accept;
   }
-  float* out = a.out + b * a.bs_out;
-  for (int i = threadIdx.x; i < a.n; i += blockDim.x) out[i] = src[i] * s;
+  __syncthreads();
+  select_left(a, b, acc_s ? a.flip + b * a.bs_flip : a.cur + b * a.bs_cur, redf);
+}
+
+__global__ void phi_combine_kernel(const double* logpsi, const int8_t* sign, const double* eloc, int batch,
+                                   int pairs, double* w, double* eloc_phi, double* wt, unsigned* status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const int p = b % pairs, q = p + pairs;
+  if (sign[p] == 0 || sign[q] == 0) {
+    atomicOr(status, ST_ZEROPSI);
+    return;
+  }
+  const double wv = (double)(sign[p] * sign[q]) * exp(logpsi[q] - logpsi[p]);
+  if (!isfinite(wv)) atomicOr(status, ST_NONFINITE);
+  if (1.0 + wv == 0.0) atomicOr(status, ST_ZEROPSI);
+  w[b] = wv;
+  if (eloc) {
+    eloc_phi[b] = (eloc[p] + wv * eloc[q]) / (1.0 + wv);
+    wt[b] = (b < pairs ? 1.0 : wv) / (1.0 + wv);
+  }
 }
 
 __global__ void dot_kernel(const float* a, long long bsa, const float* bb, long long bsb, int n, double* out,
@@ -259,7 +344,7 @@ __global__ void grad_accum_kernel(const float* G, long long bsG, long long Ph, c
                                   const long long* site_half_off, const long long* site_full_off,
                                   const int* site_size, const int* site_spin, const int8_t* spins,
                                   long long spin_stride, const double* eloc, int batch, double* sumG,
-                                  double* sumGE) {
+                                  double* sumGE, const double* wt) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= Ph) return;
   const int j = elem_site[e];
@@ -267,7 +352,7 @@ __global__ void grad_accum_kernel(const float* G, long long bsG, long long Ph, c
   const int si = site_spin[j];
   double g0 = 0, g1 = 0, ge0 = 0, ge1 = 0;
   for (int c = 0; c < batch; ++c) {
-    const double v = G[c * bsG + e];
+    const double v = wt ? wt[c] * G[c * bsG + e] : (double)G[c * bsG + e];
     const double E = eloc[c];
     if (spins[c * spin_stride + si] > 0) {
       g0 += v;
@@ -321,6 +406,94 @@ __global__ void sgd_kernel(double* master, const double* grad, long long P, doub
   master[i] -= r * delta * sg;
 }
 
+// i-th bond of the sequential order: vertical (k,m)-(k+1,m) first (columns left to
+// right, top to bottom), then horizontal (k,m)-(k,m+1) (rows top to bottom).
+__device__ __forceinline__ void bond_sites(int i, int Ly, int Lx, int& p, int& q) {
+  const int nv = Lx * (Ly - 1);
+  if (i < nv) {
+    const int m = i / (Ly - 1), k = i % (Ly - 1);
+    p = k * Lx + m;
+    q = (k + 1) * Lx + m;
+  } else {
+    const int j = i - nv, k = j / (Lx - 1), m = j % (Lx - 1);
+    p = k * Lx + m;
+    q = k * Lx + m + 1;
+  }
+}
+
+__global__ void random_propose_kernel(const RandomArgs a) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.C) return;
+  const int N = a.Ly * a.Lx, nb = 2 * N - a.Ly - a.Lx;
+  const int8_t* s = a.spins + (long long)c * N;
+  int8_t* t = a.prop + (long long)c * N;
+  for (int i = 0; i < N; ++i) t[i] = s[i];
+  int K = 0;
+  for (int i = 0; i < nb; ++i) {
+    int p, q;
+    bond_sites(i, a.Ly, a.Lx, p, q);
+    K += s[p] != s[q];
+  }
+  a.Ka[c] = K;
+  a.Kb[c] = 0;
+  a.bond[c] = -1;
+  if (K == 0) return;
+  const uint4 w = philox4x32_10(make_uint4((unsigned)c + a.chain_base, (unsigned)*a.sweep, (unsigned)a.attempt,
+                                           kTagRandom),
+                                make_uint2((unsigned)(a.key & 0xffffffffull), (unsigned)(a.key >> 32)));
+  const int pick = (int)(((unsigned long long)(w.x >> 8) * (unsigned long long)K) >> 24);
+  int seen = 0;
+  for (int i = 0; i < nb; ++i) {
+    int p, q;
+    bond_sites(i, a.Ly, a.Lx, p, q);
+    if (s[p] == s[q]) continue;
+    if (seen++ == pick) {
+      t[p] = s[q];
+      t[q] = s[p];
+      a.bond[c] = i;
+      break;
+    }
+  }
+  int Kb = 0;
+  for (int i = 0; i < nb; ++i) {
+    int p, q;
+    bond_sites(i, a.Ly, a.Lx, p, q);
+    Kb += t[p] != t[q];
+  }
+  a.Kb[c] = Kb;
+}
+
+__global__ void random_accept_kernel(const RandomArgs a) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.C) return;
+  const int N = a.Ly * a.Lx;
+  int dec = -1;
+  double rho = 0.0;
+  if (a.Ka[c] > 0) {
+    const uint4 w = philox4x32_10(make_uint4((unsigned)c + a.chain_base, (unsigned)*a.sweep, (unsigned)a.attempt,
+                                             kTagRandom),
+                                  make_uint2((unsigned)(a.key & 0xffffffffull), (unsigned)(a.key >> 32)));
+    const double r = uniform24(w.y);
+    rho = (double)(a.sg_new[c] * a.sg_cur[c]) * exp(a.lp_new[c] - a.lp_cur[c]);
+    if (!isfinite(rho)) atomicOr(a.status, ST_NONFINITE);
+    const double p = fmin(1.0, rho * rho * (double)a.Ka[c] / (double)a.Kb[c]);
+    dec = r < p ? 1 : 0;
+    atomicAdd(&a.counters[0], 1ull);
+    if (dec) {
+      atomicAdd(&a.counters[1], 1ull);
+      for (int i = 0; i < N; ++i) a.spins[(long long)c * N + i] = a.prop[(long long)c * N + i];
+      a.lp_cur[c] = a.lp_new[c];
+      a.sg_cur[c] = a.sg_new[c];
+    }
+  }
+  if (a.tr_bond) {
+    const long long o = (long long)c * a.tr_stride + a.attempt;
+    a.tr_bond[o] = a.bond[c];
+    a.tr_ratio[o] = rho;
+    a.tr_dec[o] = (int8_t)dec;
+  }
+}
+
 inline int grid_for(long long n) {
   long long g = (n + 255) / 256;
   return (int)(g > 1048576 ? 1048576 : (g < 1 ? 1 : g));
@@ -367,6 +540,17 @@ cudaError_t k_metropolis(const MetropolisArgs& a, int batch, cudaStream_t st) {
   metropolis_kernel<<<batch, kThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
+cudaError_t k_phi_decide(const MetropolisArgs& a, int batch, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  phi_decide_kernel<<<batch, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t k_phi_combine(const double* logpsi, const int8_t* sign, const double* eloc, int batch, int pairs,
+                          double* w, double* eloc_phi, double* wt, unsigned* status, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  phi_combine_kernel<<<(batch + 127) / 128, 128, 0, st>>>(logpsi, sign, eloc, batch, pairs, w, eloc_phi, wt, status);
+  return cudaGetLastError();
+}
 cudaError_t k_dot(const float* a, long long bsa, const float* b, long long bsb, int n, double* out, int batch,
                   unsigned* status, cudaStream_t st) {
   if (g_dry_run) return cudaSuccess;
@@ -397,11 +581,11 @@ cudaError_t k_logpsi(const float* x, long long bs, const int* exps, const double
 cudaError_t k_grad_accum(const float* G, long long bsG, long long Ph, const int* elem_site,
                          const long long* site_half_off, const long long* site_full_off, const int* site_size,
                          const int* site_spin, const int8_t* spins, long long spin_stride, const double* eloc,
-                         int batch, double* sumG, double* sumGE, cudaStream_t st) {
+                         int batch, double* sumG, double* sumGE, cudaStream_t st, const double* wt) {
   if (g_dry_run) return cudaSuccess;
   grad_accum_kernel<<<(int)((Ph + 255) / 256), 256, 0, st>>>(G, bsG, Ph, elem_site, site_half_off, site_full_off,
                                                              site_size, site_spin, spins, spin_stride, eloc, batch,
-                                                             sumG, sumGE);
+                                                             sumG, sumGE, wt);
   return cudaGetLastError();
 }
 cudaError_t k_energy_accum(const double* eloc, int batch, double* sums, cudaStream_t st) {
@@ -413,6 +597,16 @@ cudaError_t k_grad_final(const double* sumG, const double* sumGE, const double* 
                          cudaStream_t st) {
   if (g_dry_run) return cudaSuccess;
   grad_final_kernel<<<(int)((P + 255) / 256), 256, 0, st>>>(sumG, sumGE, sums, P, grad);
+  return cudaGetLastError();
+}
+cudaError_t k_random_propose(const RandomArgs& a, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  random_propose_kernel<<<(a.C + 127) / 128, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t k_random_accept(const RandomArgs& a, cudaStream_t st) {
+  if (g_dry_run) return cudaSuccess;
+  random_accept_kernel<<<(a.C + 127) / 128, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 cudaError_t k_sgd(double* master, const double* grad, long long P, double delta, unsigned long long key,

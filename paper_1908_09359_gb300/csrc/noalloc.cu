@@ -9,9 +9,11 @@
 // in one fixed array of device memory that the library itself defines below.
 //
 // Host code cannot use the array's name as a device address (in host code it names
-// a host-side stand-in), so the device address is looked up once per device with
-// cudaGetSymbolAddress while that device is current, and passed to the kernels.
-#include <mutex>
+// a host-side stand-in), so every call looks the device address up with
+// cudaGetSymbolAddress for the current device and context and passes it to the
+// kernels.  The lookup allocates nothing and is cheap once the library's device code is
+// loaded; doing it per call (rather than caching it per device ordinal) keeps the
+// address right after a device reset or when another context is current on the device.
 
 #include "common.cuh"
 #include "pepsvmc.h"
@@ -23,21 +25,11 @@ namespace {
 
 static __device__ __align__(256) float noalloc_scratch[PEPSVMC_NOALLOC_SCRATCH_FLOATS];
 
-constexpr int kMaxDevices = 64;
-float* scratch_addr[kMaxDevices] = {};
-std::mutex scratch_mu;
-
-// Device address of noalloc_scratch on the current device (looked up on first use).
+// Device address of noalloc_scratch in the current context.
 int scratch_on_current_device(float** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PEPSVMC_ECUDA;
-  std::lock_guard<std::mutex> lock(scratch_mu);
-  if (!scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, noalloc_scratch) != cudaSuccess || !p) return PEPSVMC_ECUDA;
-    scratch_addr[dev] = static_cast<float*>(p);
-  }
-  *out = scratch_addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, noalloc_scratch) != cudaSuccess || !p) return PEPSVMC_ECUDA;
+  *out = static_cast<float*>(p);
   return PEPSVMC_OK;
 }
 

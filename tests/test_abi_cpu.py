@@ -48,7 +48,8 @@ def _cfg(**kw):
 @pytest.mark.parametrize("bad", [dict(Ly=3, Lx=3), dict(D=0), dict(chi=0), dict(n_fit=2),
                                  dict(n_chains=0), dict(precision=7), dict(chi=64, D=16),
                                  dict(chi_measure=-1), dict(chi_measure=65), dict(chi_measure=64, D=16),
-                                 dict(chain_offset=-1), dict(wait_budget_cycles=(1 << 62) + 1)])
+                                 dict(chain_offset=-1), dict(wait_budget_cycles=(1 << 62) + 1),
+                                 dict(symmetrize=2), dict(symmetrize=1, n_chains=3)])
 def test_invalid_config_is_rejected_before_any_cuda_call(lib, bad):
     cfg = _cfg(**bad)
     t = np.zeros(10)
@@ -62,7 +63,7 @@ def test_invalid_config_is_rejected_before_any_cuda_call(lib, bad):
 
 def test_reserved_fields_must_be_zero(lib):
     cfg = _cfg()
-    cfg.reserved[2] = 1
+    cfg.reserved[1] = 1
     t = np.zeros(10)
     ctx = C.c_void_p()
     rc = lib.pepsvmc_init(C.byref(cfg), t.ctypes.data_as(C.POINTER(C.c_double)),
@@ -87,5 +88,6 @@ def test_config_layout_matches_header():
     """The ctypes mirror of pepsvmc_config has the C struct's field offsets."""
     offs = {name: getattr(_lib.Config, name).offset for name, _ in _lib.Config._fields_}
     assert offs["J1"] == 24 and offs["seed"] == 40 and offs["chi_measure"] == 52
-    assert offs["wait_budget_cycles"] == 56 and offs["chain_offset"] == 64 and offs["reserved"] == 68
+    assert offs["wait_budget_cycles"] == 56 and offs["chain_offset"] == 64 and offs["symmetrize"] == 68
+    assert offs["reserved"] == 72
     assert C.sizeof(_lib.Config) == 80

@@ -39,7 +39,8 @@ def test_default_arguments():
     assert a.case is None and a.study is None
 
 
-def test_traffic_hash_is_of_the_named_source():
-    t = bench.NCU_TRAFFIC["fused4"]
-    assert os.path.exists(os.path.join(bench.ROOT, t["source"]))
-    assert len(bench.source_sha(t["source"])) == 16
+def test_traffic_records_name_their_sources_and_summaries():
+    for t in bench.NCU_TRAFFIC.values():
+        assert os.path.exists(os.path.join(bench.ROOT, t["source"]))
+        assert os.path.exists(os.path.join(bench.ROOT, t["summary"]))
+        assert len(bench.source_sha(t["source"])) == 16 and t["bytes_per_chain"] > 0

@@ -125,7 +125,7 @@ def test_fused_whole_path_matches_oracle(torch_mod):
 
 # ------------------------------------------------------------------ four-line step
 
-def step4(torch, ctx, dims, seed, fused=True):
+def step4(torch, ctx, dims, seed, fused=True, bmajor=False):
     n, cT, cB, cT2, cB2, D1l, D1r, Du1, Dd1, D2l, D2r, Dd2 = dims
     rng = np.random.default_rng(seed)
     f32 = lambda *s: rng.standard_normal(s).astype(np.float32)  # noqa: E731
@@ -133,8 +133,15 @@ def step4(torch, ctx, dims, seed, fused=True):
              A2=f32(2, D2l, D2r, Dd1, Dd2), B=f32(n, cB, Dd2, cB2),
              s1=rng.choice(np.array([1, -1], dtype=np.int8), n), s2=rng.choice(np.array([1, -1], dtype=np.int8), n))
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
-    out = torch.full((n, cT2, D1r, D2r, cB2), float("nan"), dtype=torch.float32, device="cuda")
     ctx.set_fused(fused)
+    if bmajor:  # E at [b][a][l1][l2], out at [b'][a'][r1][r2]
+        out = torch.full((n, cB2, cT2, D1r, D2r), float("nan"), dtype=torch.float32, device="cuda")
+        ctx.env4_left(dev(c["E"].transpose(0, 4, 1, 2, 3)), dev(c["T"]), dev(c["A1"].transpose(0, 1, 3, 2, 4)),
+                      dev(c["s1"]), dev(c["A2"].transpose(0, 1, 3, 2, 4)), dev(c["s2"]), dev(c["B"]), out, dims,
+                      bmajor=True)
+        torch.cuda.synchronize()
+        return c, out.cpu().numpy().transpose(0, 2, 3, 4, 1)
+    out = torch.full((n, cT2, D1r, D2r, cB2), float("nan"), dtype=torch.float32, device="cuda")
     ctx.env4_left(dev(c["E"]), dev(c["T"]), dev(c["A1"].transpose(0, 1, 3, 2, 4)), dev(c["s1"]),
                   dev(c["A2"].transpose(0, 1, 3, 2, 4)), dev(c["s2"]), dev(c["B"]), out, dims)
     torch.cuda.synchronize()
@@ -147,6 +154,7 @@ def oracle_step4(c, i):
                          f(c["A2"][0 if c["s2"][i] > 0 else 1]), f(c["B"][i]))
 
 
+@pytest.mark.parametrize("bmajor", [False, True])
 @pytest.mark.parametrize("precision", [3, 1])
 @pytest.mark.parametrize("dims", [
     (160, 32, 32, 32, 32, 8, 8, 8, 8, 8, 8, 8),   # 24x24 bulk row pair: four a' tiles, 16 b tiles
@@ -155,13 +163,13 @@ def oracle_step4(c, i):
     (11, 9, 7, 11, 13, 3, 2, 4, 2, 3, 2, 2),      # every bond different
     (13, 1, 1, 4, 3, 1, 4, 1, 4, 1, 4, 4),        # left edge of the top row pair
 ])
-def test_fused_env4_matches_oracle_elementwise(torch_mod, precision, dims):
+def test_fused_env4_matches_oracle_elementwise(torch_mod, precision, dims, bmajor):
     from paper_1908_09359_gb300 import api
     n = dims[0]
     D, chi = max(dims[5:]), max(dims[1:5])
     ctx = api.PepsVMC(8, 8, D, chi, n, inputs.peps_tensors(8, 8, D, 1), inputs.sketch(8, chi, D, 1),
                       seed=1, precision=precision)
-    c, got = step4(torch_mod, ctx, dims, sum(dims) + precision)
+    c, got = step4(torch_mod, ctx, dims, sum(dims) + precision, bmajor=bmajor)
     el_tol, nrm_tol = TOL[precision]
     for i in sorted(set(list(range(0, n, max(1, n // 6))) + [n - 1])):
         ref = oracle_step4(c, i)

@@ -152,3 +152,48 @@ def test_train_proposal_on_given_configurations(api):
     r = ctx.energy_and_grad(1)
     assert np.all(np.isfinite(r["eloc"]))
     ctx.close()
+
+
+def test_learned_against_plain_comparison(api):
+    """What the trained network gains over the plain sampler, measured the way the mixing
+    study does (8x8 shapes, bond-decay tensors, 512 chains): both arms from the same
+    thermalised configurations, tau_int of E_loc and M_z^2, raw and effective samples/s.
+    The test asserts that the comparison is produced and that the two arms sample the
+    same distribution (energies per site within five combined tau-corrected standard
+    errors); it does not assert which arm is faster."""
+    import time
+
+    from paper_1908_09359_gb300 import autocorr
+    C, sweeps, N = 512, 40, 64
+    w = structured_8x8(C)
+    ctx = api.PepsVMC(8, 8, 4, 16, C, w["tensors"], w["sketch"], seed=6)
+    ctx.set_spins(inputs.start_spins(C, 8, 8, 12, "random"))
+    ctx.sample_sweep(20)
+    start, sweep0 = ctx.get_spins(), ctx.sweep_counter
+
+    def arm():
+        ctx.set_spins(start)
+        ctx.set_sweep_counter(sweep0)
+        el, mz, secs = np.empty((sweeps, C)), np.empty((sweeps, C)), 0.0
+        for t in range(sweeps):
+            t0 = time.perf_counter()
+            el[t] = ctx.energy_and_grad(1, want_grad=False)["eloc"]
+            secs += time.perf_counter() - t0
+            mz[t] = autocorr.staggered_mz2(ctx.get_spins())
+        mean, err = autocorr.mean_and_error(el / N)
+        tau = max(autocorr.tau_int(el)[0], autocorr.tau_int(mz)[0])
+        return mean, err, tau, sweeps * C / secs
+
+    plain = arm()
+    ctx.set_proposal_params(inputs.proposal_params(3))
+    ctx.proposal_collect(8)
+    ctx.proposal_train(8, 256, 2e-3)
+    ctx.set_proposal(1)
+    learned = arm()
+    for mean, err, tau, sps in (plain, learned):
+        assert np.isfinite(mean) and err > 0 and tau > 0 and sps > 0
+    sig = np.hypot(plain[1], learned[1])
+    assert abs(plain[0] - learned[0]) <= 5 * sig, (plain, learned)
+    print("plain eff/s %.1f (tau %.3f), learned eff/s %.1f (tau %.3f)"
+          % (plain[3] / (2 * plain[2]), plain[2], learned[3] / (2 * learned[2]), learned[2]))
+    ctx.close()

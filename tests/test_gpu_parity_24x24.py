@@ -1,0 +1,103 @@
+"""Parity of the bench's form at the bench's launch: 24x24 J1-J2 (J2/J1 = 0.5), D = 8,
+Dc = 32, 512 chains in one launch, split BF16 with the fused column steps and the
+autotuned separate products, CUDA graphs on -- against the FP64 oracle on sampled chains.
+
+The tensors are the bond-decay recipe (bond weights lambda_i = exp(-i), as after App. A's
+simple update), where the truncated contraction is well conditioned; on the iid recipe of
+the throughput workload the contraction at Dc = 32 is chaotic (float32 input rounding alone
+moves ln|Psi| by 0.1-0.9 after a few sweeps), so there only the throughput is measured.
+
+Checked: for two chains, every ratio and decision of the sweep's first column (the
+oracle replays the transposed lattice's first row with its bottom environments, taking
+the GPU's decision at near-ties |ln r - ln rho^2| < 1e-5; a whole oracle sweep of this
+lattice takes over ten minutes of host time); for four chains, E_loc, ln|Psi|, sign and G
+of the measurement after the sweep.  Bounds: twice the deviation of the oracle itself run
+in emulated split BF16 at these shapes (tests/golden/float32_spread.json, written by
+tests/golden/make_float32_spread.py).  The oracle runs in six spawned single-threaded
+processes.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1908_09359_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SWEEP_CHAINS = (0, 341)
+MEASURE_CHAINS = (85, 170, 426, 511)
+SPLIT = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                    "float32_spread.json")))["split_bf16_bond_decay_24x24"]
+
+
+def _one_thread():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+
+
+def _workload():
+    w = inputs.workload("peps_24x24", n_chains=512)
+    w["tensors"] = inputs.peps_tensors(24, 24, 8, w["seed"], False, bond_decay=1.0)
+    return w
+
+
+def _oracle_job(job):
+    kind, c, spins, follow = job
+    from oracle import vmc
+    w = _workload()
+    g = vmc.unpack(w["tensors"], 24, 24, 8)
+    if kind == "sweep":
+        tr = vmc.Trace(follow=follow, tie=1e-5)
+        gT = vmc.transpose_lattice(g)
+        st = np.ascontiguousarray(spins.T).astype(np.int8)
+        Bs, _ = vmc.bottom_envs(gT, st, 32, w["sketch"], 3)
+        vmc._sample_row(gT, st, 0, vmc.trivial_mps(24), Bs[0], w["seed"], c, 7, 0, tr)
+        return kind, c, tr.rows, None
+    r = vmc.measure(g, spins, 32, w["sketch"], 3, 1.0, 0.5)
+    G = np.concatenate([x.ravel() for row in r["G"] for x in row])
+    return kind, c, (r["eloc"], r["eloc_scale"], r["logpsi"], r["sign"]), G
+
+
+def test_bench_launch_matches_oracle_on_sampled_chains():
+    import multiprocessing as mp
+
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1908_09359_gb300 import api, build
+    build.build()
+    w = _workload()
+    start = inputs.start_spins(512, 24, 24, w["seed"], "random")
+    ctx = api.PepsVMC(24, 24, 8, 32, 512, w["tensors"], w["sketch"], J1=1.0, J2=0.5, seed=w["seed"], n_fit=3,
+                      precision=api.MIXED_BF16X3)
+    ctx.set_spins(start)
+    ctx.energy_and_grad(2, want_samples=False, want_grad=False)  # autotuner, sketches, graph capture + replay
+    ctx.set_spins(start)
+    ctx.set_sweep_counter(7)
+    ctx.enable_trace(True)
+    ctx.sample_sweep(1)
+    ratio, dec = ctx.get_trace()
+    final = ctx.get_spins()
+    e, lp, sg = ctx.measure()
+    G = {c: ctx.chain_grad(c) for c in MEASURE_CHAINS}
+    ctx.close()
+    col0 = set(range(23))  # vertical bonds of column 0 (ids m*(Ly-1)+k with m = 0)
+    jobs = [("sweep", c, start[c], {b: int(dec[c, b]) for b in col0 if dec[c, b] >= 0}) for c in SWEEP_CHAINS]
+    jobs += [("measure", c, final[c], None) for c in MEASURE_CHAINS]
+    with mp.get_context("spawn").Pool(len(jobs), initializer=_one_thread) as pool:
+        res = pool.map(_oracle_job, jobs)
+    rtol = 2 * SPLIT["sweep_ratio_max"]
+    for kind, c, a, b in res:
+        if kind == "sweep":
+            assert len(a) == sum(1 for x in col0 if dec[c, x] >= 0)
+            for bond, rho, _, acc in a:
+                assert abs(ratio[c, bond] - rho) <= rtol * max(abs(rho), 1.0), (c, bond, ratio[c, bond], rho)
+                assert int(acc) == int(dec[c, bond]), (c, bond)
+        else:
+            eloc, scale, logpsi, sign = a
+            assert abs(e[c] - eloc) <= 2 * SPLIT["eloc_rel_scale_max"] * scale, (c, e[c], eloc, scale)
+            assert sg[c] == sign and abs(lp[c] - logpsi) <= 2 * SPLIT["logpsi_abs_max"], (c, lp[c], logpsi)
+            assert np.linalg.norm(G[c] - b) <= 2 * SPLIT["grad_norm_max"] * np.linalg.norm(b)
+            assert np.max(np.abs(G[c] - b)) <= 2 * SPLIT["grad_elementwise_max"] * np.max(np.abs(b))

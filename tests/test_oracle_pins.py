@@ -492,3 +492,50 @@ def test_random_nnasp_and_sequential_sweep_share_the_stationary_distribution():
     assert float(rn.stationary(Ps) @ eloc) == pytest.approx(E, abs=1e-10)
     wrong = rn.random_scheme_matrix(cfg, psi, Ly, Lx, with_k=False)
     assert np.max(np.abs(pi @ wrong - pi)) > 1e-4                      # the 1/K factors matter
+
+
+# -------------------------------------------- P11: the random-NNASP sampler (Sec. II A)
+
+def test_random_attempt_reproduces_the_transition_matrix():
+    """The Philox-driven random-NNASP attempt (Eq. (prob_r)) on 2x4 at exact Dc: for every
+    configuration and every pair index, the trial it builds and the acceptance probability
+    min[1, |Psi_b|^2 K_a / (|Psi_a|^2 K_b)] it applies equal the transition matrix entry
+    K_a P[a, b] of the exact random scheme, whose stationary law is |Psi|^2 (pinned above);
+    and a uniform just below / above that probability is accepted / rejected."""
+    from oracle import random_nnasp as rn
+    g = peps(2, 4, 2, 17)
+    W = inputs.sketch(4, 4, 2, 17)
+    cfg, psi = rn.sector(g)
+    P = rn.random_scheme_matrix(cfg, psi, 2, 4)
+    index = {c.tobytes(): n for n, c in enumerate(cfg.reshape(len(cfg), -1))}
+    for a in range(0, len(cfg), 7):
+        pairs = rn.nnasps(cfg[a].ravel(), rn.nn_bonds(2, 4))
+        K = len(pairs)
+        for i in range(K):
+            m = -(-(i << 24) // K)  # smallest 24-bit m with floor(m K / 2^24) = i
+            word = m << 8
+            assert philox.pick(word, K) == i
+            rec = []
+            new, _ = rn.attempt_with(g, cfg[a], 4, W, 1, word, 0.0, None, rec)
+            bond, rho, Ka, Kb, acc = rec[0]
+            b = index[new.tobytes()]
+            p_acc = min(1.0, rho * rho * Ka / Kb)
+            assert Ka == K and acc
+            assert p_acc == pytest.approx(K * P[a, b], rel=1e-9, abs=1e-12)
+            assert rho == pytest.approx(psi[b] / psi[a], rel=1e-9)
+            if p_acc < 1.0:
+                rec = []
+                rn.attempt_with(g, cfg[a], 4, W, 1, word, p_acc * (1 + 1e-9), None, rec)
+                assert not rec[0][4]
+            assert int(new.sum()) == int(cfg[a].sum())
+
+
+def test_random_sweep_keeps_sz_and_counts_attempts():
+    from oracle import random_nnasp as rn
+    g = peps(4, 4, 2, 3)
+    W = inputs.sketch(4, 4, 2, 3)
+    s0 = inputs.start_spins(1, 4, 4, 9, "random")[0]
+    rec = []
+    s1 = rn.random_sweep(g, s0, 4, W, 1, 5, 0, 0, record=rec)
+    assert len(rec) == 16 and int(s1.sum()) == 0
+    assert any(r[4] for r in rec)
