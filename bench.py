@@ -221,13 +221,15 @@ def binding_roofline(flops, nbytes, seconds, compute_peak, hbm_peak):
 
 def kernel_groups(shapes):
     """Per-launch-shape profile records -> totals per kernel: the fused four-line and
-    three-line steps, the separate tensor-core and FP32 products, the QR."""
+    three-line steps, the fit's fused optimal site, the separate tensor-core and FP32
+    products, the QR and the per-chain reductions (normalisations, ratios, decisions)."""
     groups = {}
     for r in shapes:
         s = r["shape"]
         g = ("fused4" if s.startswith("fused4") else "fused3" if s.startswith("fused3") else
+             "fusedP" if s.startswith("fusedP") else
              "gemm_tc" if s.startswith("gemm tc") else "gemm_f32" if s.startswith("gemm f32") else
-             "qr" if s.startswith("qr") else "other")
+             "qr" if s.startswith("qr") else "reductions" if r["flops"] == 0 else "other")
         acc = groups.setdefault(g, {"launches": 0, "flops": 0.0, "ms": 0.0})
         acc["launches"] += r["launches"]
         acc["flops"] += r["flops"]
@@ -549,13 +551,14 @@ def run_ours(args):
 
     (bf16, bf16_src), (hbm, hbm_src) = measured_peaks()
     groups = kernel_groups(shapes)
-    contraction = {k: v for k, v in groups.items() if k != "qr" and k != "other"}
+    contraction = {k: v for k, v in groups.items() if k not in ("qr", "reductions", "other")}
     dominant = max(contraction, key=lambda k: contraction[k]["ms"]) if contraction else None
     roofline = None
     if dominant:
         bulk = None
-        if dominant in ("fused4", "fused3"):
-            key = "fused4 32 32 32 32" if dominant == "fused4" else "fused3 32 32 32 32 x 8 8 8 8"
+        if dominant in ("fused4", "fused3", "fusedP"):
+            key = {"fused4": "fused4 32 32 32 32", "fused3": "fused3 32 32 32 32 x 8 8 8 8",
+                   "fusedP": "fusedP 32 32 32 32 x 8 8 8 8"}[dominant]
             bulk = next((r for r in shapes if r["shape"] == key), None)
         rec = bulk or {"shape": dominant, **contraction[dominant]}
         per_launch_flops = rec["flops"] / rec["launches"]
@@ -570,9 +573,12 @@ def run_ours(args):
         nbytes = None
         if rec["shape"].startswith("fused4"):
             nbytes = 4.0 * C * (chi * D * D * chi * 2 + 2 * chi * D * chi)
-        elif rec["shape"].startswith("fused3"):
+        elif rec["shape"].startswith("fused3") or rec["shape"].startswith("fusedP"):
             nbytes = 4.0 * C * 4 * chi * D * chi
-        achieved = per_launch_flops / (per_launch_ms / 1e3) / 1e12
+        # the binding roof of this kernel: HBM when its algorithmic intensity lies below the
+        # ridge point of the compute peak, else the compute unit
+        primary, other, _, _ = binding_roofline(per_launch_flops, nbytes or 0.0, per_launch_ms / 1e3,
+                                                (cbound, cpeak, csrc), (hbm, hbm_src))
         traffic = None
         t = NCU_TRAFFIC.get(dominant)
         if t and rec is bulk and t["source_sha"] == source_sha(t["source"]):
@@ -581,10 +587,12 @@ def run_ours(args):
         roofline = {
             "kernel": {"fused4": "env4_fused_kernel (four-line column step, tcgen05, split BF16)",
                        "fused3": "env3_fused_kernel (three-line column step, tcgen05, split BF16)",
+                       "fusedP": "proj3_fused_kernel (optimal site of the truncation fit, tcgen05, split BF16)",
                        "gemm_tc": "gemm_tc_kernel (separate products, tcgen05)",
                        "gemm_f32": "gemm_f32_kernel (separate products, FP32 CUDA cores)"}[dominant],
-            "shape": rec["shape"], "bound": cbound, "achieved": achieved, "peak": cpeak, "unit": "TFLOP/s",
-            "frac": achieved / cpeak, "peak_source": csrc, "traffic": traffic,
+            "shape": rec["shape"], "bound": primary["bound"], "achieved": primary["achieved"],
+            "peak": primary["peak"], "unit": primary["unit"], "frac": primary["frac"],
+            "peak_source": primary["peak_source"], "other_roof": other, "traffic": traffic,
             "traffic_source": (t["summary"] if traffic else "null: no ncu capture of this kernel source"),
             "flops_per_launch": per_launch_flops, "ms_per_launch": per_launch_ms,
             "algorithmic_bytes_per_launch": nbytes,

@@ -228,6 +228,34 @@ int pepsvmc_finalize_sums(pepsvmc_ctx* ctx);
  * Errors: ESTATE if no gradient was computed.                               */
 int pepsvmc_update(pepsvmc_ctx* ctx, double delta, uint64_t step);
 
+/* Simple-update imaginary-time evolution (App. A), the initialiser of the
+ * optimisation, in float64 on the GPU; needs no context.  The PEPS is held as site
+ * tensors B (packed layout of pepsvmc_init's tensors) and one vector lambda of length
+ * D on every nearest-neighbour link:
+ *   lam_h [Ly][Lx-1][D] for links (k,m)-(k,m+1), lam_v [Ly-1][Lx][D] for (k,m)-(k+1,m).
+ * One Trotter step applies exp(-tau J1 S_i.S_j) to the horizontal NN bonds with m
+ * even, then m odd, to the vertical ones with k even, then k odd, and, when J2 != 0,
+ * exp(-(tau/2) J2 S_i.S_k) to both diagonals of every plaquette through each of its
+ * two corner sites (plaquettes in four groups by the parity of (k, m)).  An NN update
+ * reduces both tensors (outer lambdas absorbed) by QR, applies the gate to the R
+ * factors joined by the bond lambda and truncates by SVD; an NNN update follows the
+ * QR / SVD / SVD steps of App. A's figure.  Each truncation keeps min(D, #{sigma >
+ * 1e-7 sigma_max}) singular values (missing entries are zero) and normalises the new
+ * lambda to unit norm; inverse lambdas are 1/lambda above 1e-14 of the largest entry,
+ * else 0.  Steps run until the mean over links of ||lambda(t+tau) - lambda(t)|| /
+ * ||lambda(t)|| is below tol or max_steps are done.
+ *   B, lam_h, lam_v: host float64, in/out (lam_h may be NULL when Lx = 1, lam_v when
+ *                    Ly = 1);
+ *   peps_out:        host float64 (nullable), the packed tensors with lambda^(1/2) of
+ *                    every link absorbed into both of its tensors, ready for
+ *                    pepsvmc_init / pepsvmc_set_tensors;
+ *   steps_done, change_out: host (nullable), the steps run and the last change.
+ * D <= 8.  Allocates and frees its own device memory; synchronous on the stream.
+ * Errors: EINVAL (sizes, null pointers), ENOMEM, ENONFINITE, ECUDA.          */
+int pepsvmc_simple_update(int32_t Ly, int32_t Lx, int32_t D, double J1, double J2, double tau,
+                          int32_t max_steps, double tol, double* B, double* lam_h, double* lam_v,
+                          double* peps_out, int32_t* steps_done, double* change_out, void* stream);
+
 /* Three-line environment step (App. C, Fig. "contraction" (c)) for n_chains chains,
  * on the context's stream, with the context's scratch:
  *   out[c](a',r,b') = sum over a,l,b,u,d of

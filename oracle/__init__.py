@@ -11,6 +11,11 @@ vmc     boundary-MPS contraction with variational truncation, three- and four-li
         environments, sequential Metropolis sweep, E_loc, G = Delta/Psi, gradient
         and sign-SGD (arXiv:1908.09359, Sec. II, Algorithm 1, App. B, App. C).
 exact   brute-force amplitudes and S^z = 0 enumeration for small lattices.
+proposal        the learned band proposal and its Metropolis-Hastings step.
+random_nnasp    the random-NNASP scheme of Sec. II A (exact transition matrices and
+                attempt-by-attempt replay).
+spin_inversion  Phi(S) = Psi(S) + Psi(S-bar): |Phi|^2 sweep, E^Phi, G^Phi (Sec. II B).
+simple_update   simple-update imaginary-time evolution with NN and NNN gates (App. A).
 
 Every function is pinned by the CPU tests (tests/test_oracle_*.py) to something
 other than itself: known-answer vectors, brute force, closed forms, invariants and

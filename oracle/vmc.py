@@ -22,6 +22,8 @@ Readings of points the paper leaves open:
   to right-orthonormal form site by site; the first left-to-right sweep is then a
   randomized range finder and later sweeps refine it.  ``n_fit`` (odd) half-sweeps
   are done; the result is left-orthonormal, normalised, its norm kept as a log.
+  The second truncation mode, SVD (``n_fit = 0``), is the canonical two-pass
+  compression of the exact product (``compress_svd``); the GPU path runs the fit.
 * QR: Householder QR with the sign of each column chosen so that diag(R) >= 0.
 * Sweep order (Sec. II A): vertical bonds first (columns left to right, bonds top
   to bottom, through the transposed lattice), then horizontal bonds (rows top to
@@ -143,12 +145,44 @@ def mpo_times_mps(T, row):
     return X
 
 
+def compress_svd(X, chi):
+    """Truncation by SVD (canonical two-pass compression): X is brought to left-orthonormal
+    form by QR (diag(R) >= 0), then, from the right, each site's (left bond, spin x right
+    bond) matrix is truncated by an SVD to the bond caps; the result is brought back to
+    left-orthonormal form and normalised.  Returns (V, log ||V||) like ``compress``."""
+    L = len(X)
+    phys = [x.shape[1] for x in X]
+    r = bond_caps([X[m].shape[2] for m in range(L - 1)], phys, chi)
+    Y = [np.array(x, dtype=np.float64) for x in X]
+    logn = 0.0
+    for sweep in range(2):
+        if sweep == 1:
+            for m in range(L - 1, 0, -1):   # right to left: truncated SVDs
+                b0, p, b1 = Y[m].shape
+                U, S, Vt = np.linalg.svd(Y[m].reshape(b0, p * b1), full_matrices=False)
+                k = min(r[m - 1], len(S))
+                Y[m] = Vt[:k].reshape(k, p, b1)
+                Y[m - 1] = np.einsum("apb,bk->apk", Y[m - 1], U[:, :k] * S[:k])
+        for m in range(L - 1):              # left to right: QR
+            b0, p, b1 = Y[m].shape
+            Q, R = qr_pos(Y[m].reshape(b0 * p, b1))
+            Y[m] = Q.reshape(b0, p, Q.shape[1])
+            Y[m + 1] = np.einsum("ab,bpc->apc", R, Y[m + 1])
+        nrm = np.linalg.norm(Y[L - 1])
+        Y[L - 1] = Y[L - 1] / nrm
+        logn += float(np.log(nrm))
+    return Y, logn
+
+
 def compress(X, chi, W, n_fit):
     """Variational fit of App. B: minimise ||X - V||^2 over MPS V of bond <= chi.
 
     Returns (V, log ||V_fit||) with V normalised and left-orthonormal (centre at the
-    last site).  ``n_fit`` is the number of one-site half-sweeps (odd).
+    last site).  ``n_fit`` is the number of one-site half-sweeps (odd); ``n_fit = 0``
+    selects the SVD truncation of ``compress_svd`` instead of the fit.
     """
+    if n_fit == 0:
+        return compress_svd(X, chi)
     if n_fit < 1 or n_fit % 2 == 0:
         raise ValueError("n_fit must be odd")
     L = len(X)

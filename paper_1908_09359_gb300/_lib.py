@@ -34,7 +34,7 @@ SYMBOLS = [
     "pepsvmc_proposal_logits", "pepsvmc_proposal_collect", "pepsvmc_proposal_dataset_size", "pepsvmc_proposal_load",
     "pepsvmc_proposal_train", "pepsvmc_train_proposal", "pepsvmc_set_proposal", "pepsvmc_learned_sweep", "pepsvmc_get_learned_trace",
     "pepsvmc_env4_left", "pepsvmc_set_fused", "pepsvmc_random_sweep", "pepsvmc_get_random_trace", "pepsvmc_set_wait_budget", "pepsvmc_get_sums", "pepsvmc_set_sums", "pepsvmc_sums_device", "pepsvmc_finalize_sums",
-    "pepsvmc_get_phi",
+    "pepsvmc_get_phi", "pepsvmc_simple_update",
 ]
 
 
@@ -118,6 +118,8 @@ def load(path: str | None = None):
         "pepsvmc_sums_device": (C.c_int, [P, C.POINTER(P), C.POINTER(P), C.POINTER(P)]),
         "pepsvmc_finalize_sums": (C.c_int, [P]),
         "pepsvmc_get_phi": (C.c_int, [P, D, D]),
+        "pepsvmc_simple_update": (C.c_int, [I32, I32, I32, C.c_double, C.c_double, C.c_double, I32, C.c_double,
+                                            D, D, D, D, C.POINTER(C.c_int32), D, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

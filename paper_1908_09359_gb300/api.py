@@ -345,3 +345,26 @@ def env3_left_noalloc(E, T, A, spins, B, out, dims, stream=None):
     if rc != 0:
         raise PepsvmcError(rc, "pepsvmc_env3_left_noalloc failed (sizes beyond the fixed scratch, "
                                "null pointers or a CUDA error)")
+
+
+def simple_update(Ly, Lx, D, B, lam_h, lam_v, J1=1.0, J2=0.0, tau=0.01, max_steps=100, tol=1e-11, stream=None):
+    """Simple-update imaginary-time evolution (pepsvmc_simple_update) from the packed site
+    tensors B and link vectors lam_h (Ly, Lx-1, D), lam_v (Ly-1, Lx, D).  Returns
+    (B, lam_h, lam_v, peps, steps, change): the evolved state, the Monte Carlo tensors
+    with lambda^(1/2) absorbed, the steps run and the last mean relative lambda change."""
+    lib = _lib.load()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    b = np.ascontiguousarray(B, dtype=np.float64).copy()
+    lh = np.ascontiguousarray(lam_h, dtype=np.float64).reshape(Ly, max(Lx - 1, 0), D).copy()
+    lv = np.ascontiguousarray(lam_v, dtype=np.float64).reshape(max(Ly - 1, 0), Lx, D).copy()
+    out = np.empty_like(b)
+    steps = C.c_int32()
+    change = C.c_double()
+    rc = lib.pepsvmc_simple_update(int(Ly), int(Lx), int(D), float(J1), float(J2), float(tau), int(max_steps),
+                                   float(tol), _dp(b), _dp(lh), _dp(lv), _dp(out), C.byref(steps), C.byref(change),
+                                   C.c_void_p(stream))
+    if rc != 0:
+        raise PepsvmcError(rc, "pepsvmc_simple_update failed")
+    return b, lh, lv, out, steps.value, change.value

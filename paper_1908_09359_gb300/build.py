@@ -19,6 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(OUT, "libpepsvmc.so")
 
 SOURCES = ["contract_f32.cu", "contract_tc.cu", "fused_env3.cu", "fused_env4.cu", "qr.cu", "kernels.cu", "engine.cu", "noalloc.cu",
+           "simple_update.cu",
            "proposal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

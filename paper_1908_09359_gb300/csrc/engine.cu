@@ -264,7 +264,7 @@ struct pepsvmc_ctx {
     for (const Pending& p : pending) {
       float ms = 0.f;
       PV_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
-      prof_acc[p.kind == 0 ? 2 : 4] += ms;
+      if (p.kind < 2) prof_acc[p.kind == 0 ? 2 : 4] += ms;  // kind 2: per-chain reductions (shape table only)
       ShapeStat& ss = shape_stats[p.shape];
       ss.n += 1;
       ss.flops += p.flops;
@@ -431,7 +431,7 @@ struct pepsvmc_ctx {
     if (!chains(a, bsa, n, 4, "dot a") || !chains(b, bsb, n, 4, "dot b") || !chains(out, 1, 1, 8, "dot out"))
       return cudaErrorInvalidValue;
     ++launches;
-    return k_dot(a, bsa, b, bsb, n, out, C, status, st);
+    return timed(2, [&] { return k_dot(a, bsa, b, bsb, n, out, C, status, st); }, "dot");
   }
 
   // rho_export (nullable): [chain][2][Ly][Lx] receives each NN ratio at (channel, site).
@@ -443,15 +443,17 @@ struct pepsvmc_ctx {
       return cudaErrorInvalidValue;
     ++launches;
     float* ro = (rho_export && export_idx >= 0) ? rho_export : nullptr;
-    return k_ratio_accum(a, bsa, b, bsb, n, den, spins, (long long)Ly * Lx, si, sj, halfJ, eloc, C, status, st, ro,
-                         2LL * Ly * Lx, export_idx);
+    return timed(2, [&] {
+      return k_ratio_accum(a, bsa, b, bsb, n, den, spins, (long long)Ly * Lx, si, sj, halfJ, eloc, C, status, st, ro,
+                           2LL * Ly * Lx, export_idx);
+    }, "ratio_accum");
   }
 
   cudaError_t logpsi_of(const float* x, long long bs, const double* logT, const double* logB) {
     if (!chains(x, bs, 1, 4, "logpsi x") || !chains(logT, 1, 1, 8, "logT") || !chains(logB, 1, 1, 8, "logB"))
       return cudaErrorInvalidValue;
     ++launches;
-    return k_logpsi(x, bs, exps, logT, logB, logpsi, sign, C, status, st);
+    return timed(2, [&] { return k_logpsi(x, bs, exps, logT, logB, logpsi, sign, C, status, st); }, "logpsi");
   }
 
   const int8_t* sel_base = nullptr;  // spin array the site tensors are selected from (default: spins)
@@ -962,7 +964,8 @@ struct pepsvmc_ctx {
         (x3 && !chains(x3, bs, n3, 4, "normalize x3")))
       return cudaErrorInvalidValue;
     ++launches;
-    return k_normalize_pow2(x, bs, n, x2, bs, n2, x3, bs, n3, ex, C, status, st);
+    return timed(2, [&] { return k_normalize_pow2(x, bs, n, x2, bs, n2, x3, bs, n3, ex, C, status, st); },
+                 "normalize_pow2");
   }
 
   // ------------------------------------------------------ boundary MPS (App. B)
@@ -1089,7 +1092,8 @@ struct pepsvmc_ctx {
         !chains(Tin.logs, 1, 1, 8, "mps log in"))
       return cudaErrorInvalidValue;
     ++launches;
-    return k_mps_normalize(center, S, vb[L - 1] * p[L - 1], exps, Tin.logs, log_out, C, status, st);
+    return timed(2, [&] { return k_mps_normalize(center, S, vb[L - 1] * p[L - 1], exps, Tin.logs, log_out, C,
+                                                 status, st); }, "mps_normalize");
   }
 
   // All top environments of orientation o (rows 1..Ly_o-1 into store, one slot per row).
@@ -1198,11 +1202,11 @@ struct pepsvmc_ctx {
           ma.phi_w = phi_w;
           ma.pairs = pairs;
           launches += 2;
-          PV_CUDA(k_metropolis(ma, C, st));
-          PV_CUDA(k_phi_decide(ma, C, st));
+          PV_CUDA(timed(2, [&] { return k_metropolis(ma, C, st); }, "metropolis"));
+          PV_CUDA(timed(2, [&] { return k_phi_decide(ma, C, st); }, "phi_decide"));
         } else {
           ++launches;
-          PV_CUDA(k_metropolis(ma, C, st));
+          PV_CUDA(timed(2, [&] { return k_metropolis(ma, C, st); }, "metropolis"));
         }
         Lin = l3[0];
         bsL = S;

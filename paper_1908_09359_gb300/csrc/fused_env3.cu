@@ -45,7 +45,11 @@ constexpr uint32_t SZ_W = 128 * 128, OFF_W = 0;               // X (S2 A, swizzl
 constexpr uint32_t SZ_E = 128 * 64, OFF_E = OFF_W + 2 * SZ_W;   // S1 A: 128 rows x 32 K
 constexpr uint32_t SZ_T = 64 * 64, OFF_T = OFF_E + 2 * SZ_E;    // S1 B: 64 rows x 32 K
 constexpr uint32_t SZ_A = 64 * 128, OFF_A = OFF_T + 2 * SZ_T;   // S2 B: 64 rows x 64 K
-constexpr uint32_t SZ_B = 32 * 256, OFF_B = OFF_A + 2 * SZ_A;   // S3 B: 32 rows x 128 K, two buffers
+// S3 B: 32 rows (b') x 128 K ((b,d)) in the 128-byte swizzled layout, two K atoms of 64;
+// with X3 the lo rows follow the hi rows inside each atom (one operand of 64 rows), so an
+// atom holds 64 rows x 128 bytes.  Two buffers.
+constexpr uint32_t SZ_B = 32 * 256, OFF_B = OFF_A + 2 * SZ_A;
+constexpr uint32_t B_ATOM = 64 * 128, B_LO = 32 * 128;
 constexpr uint32_t SMEM_USED = OFF_B + 4 * SZ_B;
 constexpr uint32_t SMEM_BYTES = SMEM_USED + 1024;  // slack to align the swizzled tile to 1 KB
 constexpr uint32_t TMEM_COLS = 256;
@@ -83,6 +87,18 @@ struct Slice {
   float b[2][8];
 };
 
+// (b', b within the tile) of B-slice unit u: lanes along b' when b' is contiguous, else
+// along b.
+__device__ __forceinline__ void b_slot(const Env3Fused& a, int u, int& b2, int& bl) {
+  if (a.sBb2 == 1 || a.sBb != 1) {
+    b2 = u & 31;
+    bl = u >> 5;
+  } else {
+    bl = u & 15;
+    b2 = u >> 4;
+  }
+}
+
 // E slice lanes: l fastest, then the b pair, then the K chunk.  The eight lanes of one
 // shared-memory store phase then write rows of eight different l, i.e. eight different
 // 16-byte bank groups of the K-major tile, and the global reads of one K value cover
@@ -112,10 +128,14 @@ __device__ __forceinline__ void fetch_slice(const Env3Fused& a, int c, int j, in
       }
     }
   }
+  // B slice lanes along whichever of b' and b is contiguous in memory (the right step
+  // reads a mirrored view whose b is contiguous); the swizzled operand layout keeps the
+  // shared-memory stores conflict-free either way
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const int u = tid + i * kThreads;
-    const int b2 = u & 31, b = j * kBT + (u >> 5);
+    int b2, bl;
+    b_slot(a, tid + i * kThreads, b2, bl);
+    const int b = j * kBT + bl;
     const bool rv = b2 < a.cB2 && b < a.cB;
     const float* src = B + b * a.sBb + b2 * a.sBb2;
 #pragma unroll
@@ -129,40 +149,55 @@ __device__ __forceinline__ void store_e(uint8_t* sm, int tid, const Slice& s) {
 #pragma unroll
   for (int i = 0; i < 2; ++i) put16<2, X3>(sm + OFF_E + kmajor_off((2 * bp + i) * 8 + l, kc * 8, 4), s.e[i], SZ_E);
 }
+// chunk (row b', K chunk b) of the swizzled S3 B operand
+__device__ __forceinline__ uint32_t b_off(int b2, int b) { return (uint32_t)(b >> 3) * B_ATOM + sw128_chunk_off(b2, b & 7); }
+
 template <bool X3>
-__device__ __forceinline__ void store_b(uint8_t* sm, int buf, int tid, const Slice& s) {
+__device__ __forceinline__ void store_b(const Env3Fused& a, uint8_t* sm, int buf, int tid, const Slice& s) {
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const int u = tid + i * kThreads;
-    put16<2, X3>(sm + OFF_B + buf * 2 * SZ_B + kmajor_off(u & 31, (u >> 5) * 8, 16), s.b[i], SZ_B);
+    int b2, bl;
+    b_slot(a, tid + i * kThreads, b2, bl);
+    put16<2, X3>(sm + OFF_B + buf * 2 * SZ_B + b_off(b2, bl), s.b[i], B_LO);
   }
 }
 
 // T tile of unit (c, t) (S1 B: rows a'_loc*8 + u, K = a) and the chain's A_s (S2 B: rows
-// r*8 + d, K = l*8 + u), straight from global memory.
-template <bool X3>
-__device__ __forceinline__ void load_unit(const Env3Fused& a, uint8_t* sm, int c, int t, int tid) {
+// r*8 + d, K = l*8 + u): fetched into registers (during the previous unit's last
+// epilogue), then stored as operands.
+struct UnitRegs {
+  float t[8];
+  float a[2][8];
+};
+__device__ __forceinline__ void fetch_unit(const Env3Fused& a, int c, int t, int tid, UnitRegs& r) {
   const float* T = a.T + (long long)c * a.bsT;
   const int row = tid & 63, kc = tid >> 6;
   const int a2 = t * kAT + (row >> 3), uu = row & 7;
   const bool rv = a2 < a.cT2 && uu < a.Du;
-  float v[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int k = kc * 8 + e;
-    v[e] = (rv && k < a.cT) ? T[k * a.sTa + uu * a.sTu + a2 * a.sTa2] : 0.f;
+    r.t[e] = (rv && k < a.cT) ? T[k * a.sTa + uu * a.sTu + a2 * a.sTa2] : 0.f;
   }
-  put16<2, X3>(sm + OFF_T + kmajor_off(row, kc * 8, 4), v, SZ_T);
   const int slot = a.sel ? (((a.sel[(long long)c * a.sel_stride] < 0) ? 1 : 0) ^ a.sel_xor) : 0;
   const float* A = a.A + (long long)slot * a.ssA;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const int u = tid + i * kThreads;
-    const int rw = u & 63, l = u >> 6, r = rw >> 3, d = rw & 7;
-    const bool ok = r < a.Dr && d < a.Dd && l < a.Dl;
+    const int rw = u & 63, l = u >> 6, rr = rw >> 3, d = rw & 7;
+    const bool ok = rr < a.Dr && d < a.Dd && l < a.Dl;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = (ok && e < a.Du) ? A[l * a.sAl + e * a.sAu + r * a.sAr + d * a.sAd] : 0.f;
-    put16<2, X3>(sm + OFF_A + kmajor_off(rw, l * 8, 8), v, SZ_A);
+    for (int e = 0; e < 8; ++e) r.a[i][e] = (ok && e < a.Du) ? A[l * a.sAl + e * a.sAu + rr * a.sAr + d * a.sAd] : 0.f;
+  }
+}
+template <bool X3>
+__device__ __forceinline__ void store_unit(uint8_t* sm, int tid, const UnitRegs& r) {
+  const int row = tid & 63, kc = tid >> 6;
+  put16<2, X3>(sm + OFF_T + kmajor_off(row, kc * 8, 4), r.t, SZ_T);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int u = tid + i * kThreads;
+    put16<2, X3>(sm + OFF_A + kmajor_off(u & 63, (u >> 6) * 8, 8), r.a[i], SZ_A);
   }
 }
 
@@ -202,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 2) env3_fused_kernel(const Env3Fused
   Slice nxt;
   fetch_slice(a, unit_of(blockIdx.x, n_at).c, 0, tid, nxt);
   store_e<X3>(sm, tid, nxt);
-  store_b<X3>(sm, 0, tid, nxt);
+  store_b<X3>(a, sm, 0, tid, nxt);
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
@@ -215,9 +250,15 @@ __global__ void __launch_bounds__(kThreads, 2) env3_fused_kernel(const Env3Fused
   int failed = -1;
   uint32_t fphase = 0, blk = 0, uph = 0;
 
+  UnitRegs ur;
+  {
+    const Unit first = unit_of(blockIdx.x, n_at);
+    fetch_unit(a, first.c, first.t, tid, ur);
+  }
   for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, uph ^= 1u) {
     const Unit cur = unit_of(u, n_at);
-    load_unit<X3>(a, sm, cur.c, cur.t, tid);
+    // T and A of this unit (the previous unit's S1 and S2 have completed)
+    store_unit<X3>(sm, tid, ur);
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
@@ -283,19 +324,24 @@ __global__ void __launch_bounds__(kThreads, 2) env3_fused_kernel(const Env3Fused
         tc_after_sync();
         const uint32_t bb = sbase + OFF_B + buf * 2 * SZ_B;
         for (int ks = 0; ks < 8; ++ks)
-          mma<2>(tmem + COL_S3, sdesc(sbase + OFF_W + ks * 256, 128, 2048), sdesc(bb + ks * 256, 128, 2048), id3,
-                 (j > 0 || ks > 0) ? 1u : 0u);
+          mma<2>(tmem + COL_S3, sdesc(sbase + OFF_W + ks * 256, 128, 2048),
+                 sdesc_sw128(bb + (ks >> 2) * B_ATOM + (ks & 3) * 32), id3, (j > 0 || ks > 0) ? 1u : 0u);
         if (j + 1 == n_bt) commit(&bar[2]);
       }
       // the other B buffer was last read by S3 of the previous tile, complete since bar[0]
       if (more) {
-        store_b<X3>(sm, buf ^ 1, tid, nxt);
+        store_b<X3>(a, sm, buf ^ 1, tid, nxt);
         fence_async_smem();
       }
       tc_before_sync();
       __syncthreads();
     }
     if (!ok) break;
+    // T and A of the next unit, in flight during this unit's final epilogue
+    if (u + (int)gridDim.x < n_units) {
+      const Unit nu = unit_of(u + gridDim.x, n_at);
+      fetch_unit(a, nu.c, nu.t, tid, ur);
+    }
     if (!(ok = block_wait(&bar[2], uph, budget))) {
       failed = 2;
       fphase = uph;
@@ -443,20 +489,32 @@ __device__ __forceinline__ void p_store_r(uint8_t* sm, int buf, int tid, const P
 // L slice of unit (c, vt) (S1 A: rows v*8 + l, K = a) and the chain's A_s (S2 B).
 template <bool X3>
 __device__ __forceinline__ void p_load_unit(const Proj3Fused& a, uint8_t* sm, int c, int vt, int tid) {
+  // lanes: l fastest, then a pair of v, then the K chunk (the three-line step's E-slice
+  // mapping: conflict-free shared-memory stores, full sectors when v is contiguous)
   const float* L = a.L + (long long)c * a.bsL;
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int u = tid + i * kThreads;
-    const int vl = u & 15, l = (u >> 4) & 7, kc = u >> 7;
-    const int v = vt * kPV + vl;
-    const bool rv = v < a.cV && l < a.Dl;
-    float x[8];
+  {
+    const int l = tid & 7, vp = (tid >> 3) & 7, kc = tid >> 6;
+    const int v0 = vt * kPV + 2 * vp;
+    const bool lv = l < a.Dl;
+    const float* src = L + (long long)v0 * a.sLv + l * a.sLl;
+    const bool vec = a.sLv == 1 && ((a.sLl | a.sLa | a.bsL) & 1) == 0 && (reinterpret_cast<uintptr_t>(a.L) & 7) == 0 &&
+                     v0 + 1 < a.cV;
+    float x[2][8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int k = kc * 8 + e;
-      x[e] = (rv && k < a.cT) ? L[k * a.sLa + l * a.sLl + v * a.sLv] : 0.f;
+      const bool kv = lv && k < a.cT;
+      if (vec) {
+        const float2 w = kv ? *reinterpret_cast<const float2*>(src + k * a.sLa) : make_float2(0.f, 0.f);
+        x[0][e] = w.x;
+        x[1][e] = w.y;
+      } else {
+        x[0][e] = (kv && v0 < a.cV) ? src[k * a.sLa] : 0.f;
+        x[1][e] = (kv && v0 + 1 < a.cV) ? src[k * a.sLa + a.sLv] : 0.f;
+      }
     }
-    put16<2, X3>(sm + P_OFF_L + kmajor_off(vl * 8 + l, kc * 8, 4), x, P_SZ_L);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) put16<2, X3>(sm + P_OFF_L + kmajor_off((2 * vp + i) * 8 + l, kc * 8, 4), x[i], P_SZ_L);
   }
   const int slot = a.sel ? ((a.sel[(long long)c * a.sel_stride] < 0) ? 1 : 0) : 0;
   const float* A = a.A + (long long)slot * a.ssA;

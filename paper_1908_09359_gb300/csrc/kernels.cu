@@ -51,6 +51,61 @@ __device__ __forceinline__ float block_max(float v, float* red) {
   return m;
 }
 
+// Per-chain vector primitives of the block reductions: 16-byte loads when both arrays
+// start on a 16-byte boundary and n is a multiple of 4, else scalar loads.
+__device__ __forceinline__ bool vec4_ok(const void* x, const void* y, int n) {
+  return (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) == 0) && (n & 3) == 0;
+}
+// this thread's part of sum_i x[i] y[i] in float64
+__device__ __forceinline__ double part_dot(const float* x, const float* y, int n) {
+  double s = 0.0;
+  if (vec4_ok(x, y, n)) {
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+    for (int i = threadIdx.x; i < (n >> 2); i += blockDim.x) {
+      const float4 a = x4[i], b = y4[i];
+      s += (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
+    }
+  } else {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)x[i] * y[i];
+  }
+  return s;
+}
+// this thread's part of max |x[i]|; *bad set when an entry is not finite
+__device__ __forceinline__ float part_maxabs(const float* x, int n, bool* bad) {
+  float mx = 0.f;
+  bool nf = false;
+  if (vec4_ok(x, x, n)) {
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (int i = threadIdx.x; i < (n >> 2); i += blockDim.x) {
+      const float4 a = x4[i];
+      nf |= !isfinite(a.x) || !isfinite(a.y) || !isfinite(a.z) || !isfinite(a.w);
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))));
+    }
+  } else {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float v = x[i];
+      nf |= !isfinite(v);
+      mx = fmaxf(mx, fabsf(v));
+    }
+  }
+  if (bad) *bad = nf;
+  return mx;
+}
+// dst[i] = src[i] * f (dst may equal src)
+__device__ __forceinline__ void scale_copy(float* dst, const float* src, int n, float f) {
+  if (vec4_ok(dst, src, n)) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    for (int i = threadIdx.x; i < (n >> 2); i += blockDim.x) {
+      const float4 a = s4[i];
+      d4[i] = make_float4(a.x * f, a.y * f, a.z * f, a.w * f);
+    }
+  } else {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i] * f;
+  }
+}
+
 __global__ void fill_kernel(float* p, long long n, float v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     p[i] = v;
@@ -71,13 +126,8 @@ __global__ void normalize_pow2_kernel(float* x, long long bs, int n, float* x2, 
   __shared__ float red[kThreads / 32];
   const int b = blockIdx.x;
   float* xb = x + b * bs;
-  float mx = 0.f;
   bool bad = false;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float v = xb[i];
-    if (!isfinite(v)) bad = true;
-    mx = fmaxf(mx, fabsf(v));
-  }
+  float mx = part_maxabs(xb, n, &bad);
   if (__syncthreads_or(bad)) {
     if (threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
     return;
@@ -90,15 +140,9 @@ __global__ void normalize_pow2_kernel(float* x, long long bs, int n, float* x2, 
   int e;
   frexpf(mx, &e);
   const float s = ldexpf(1.f, -e);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xb[i] *= s;
-  if (x2) {
-    float* p = x2 + b * bs2;
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) p[i] *= s;
-  }
-  if (x3) {
-    float* p = x3 + b * bs3;
-    for (int i = threadIdx.x; i < n3; i += blockDim.x) p[i] *= s;
-  }
+  scale_copy(xb, xb, n, s);
+  if (x2) scale_copy(x2 + b * bs2, x2 + b * bs2, n2, s);
+  if (x3) scale_copy(x3 + b * bs3, x3 + b * bs3, n3, s);
   if (exps && threadIdx.x == 0) exps[b] += e;
 }
 
@@ -107,8 +151,7 @@ __global__ void mps_normalize_kernel(float* x, long long bs, int n, const int* e
   __shared__ double red[kThreads / 32];
   const int b = blockIdx.x;
   float* xb = x + b * bs;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)xb[i] * xb[i];
+  double s = part_dot(xb, xb, n);
   s = block_sum(s, red);
   if (!(s > 0.0) || !isfinite(s)) {
     if (threadIdx.x == 0) atomicOr(status, isfinite(s) ? ST_ZEROPSI : ST_NONFINITE);
@@ -116,7 +159,7 @@ __global__ void mps_normalize_kernel(float* x, long long bs, int n, const int* e
   }
   const double nrm = sqrt(s);
   const float inv = (float)(1.0 / nrm);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xb[i] *= inv;
+  scale_copy(xb, xb, n, inv);
   if (threadIdx.x == 0) {
     const double li = log_in ? log_in[b] : 0.0;
     log_out[b] = li + log(nrm) + (exps ? exps[b] * 0.6931471805599453 : 0.0);
@@ -125,8 +168,7 @@ __global__ void mps_normalize_kernel(float* x, long long bs, int n, const int* e
 
 // L(m) of the chosen configuration (src), scaled by a power of two to max |.| in [1/2, 1).
 __device__ void select_left(const MetropolisArgs& a, int b, const float* src, float* redf) {
-  float mx = 0.f;
-  for (int i = threadIdx.x; i < a.n; i += blockDim.x) mx = fmaxf(mx, fabsf(src[i]));
+  float mx = part_maxabs(src, a.n, nullptr);
   mx = block_max(mx, redf);
   float s = 1.f;
   if (mx > 0.f && isfinite(mx)) {
@@ -134,8 +176,7 @@ __device__ void select_left(const MetropolisArgs& a, int b, const float* src, fl
     frexpf(mx, &e);
     s = ldexpf(1.f, -e);
   }
-  float* out = a.out + b * a.bs_out;
-  for (int i = threadIdx.x; i < a.n; i += blockDim.x) out[i] = src[i] * s;
+  scale_copy(a.out + b * a.bs_out, src, a.n, s);
 }
 
 // Sequential Metropolis step on one pair (Eq. (9)) for every chain.
@@ -150,11 +191,10 @@ __global__ void metropolis_kernel(const MetropolisArgs a) {
   const float* Rf = a.Rflip + b * a.bs_Rflip;
   int8_t* sp = a.spins + b * a.spin_stride;
   const bool anti = sp[a.site_a] != sp[a.site_b];
-  double den = 0.0, num = 0.0;
-  for (int i = threadIdx.x; i < a.n; i += blockDim.x) den += (double)cur[i] * Rc[i];
+  double den = part_dot(cur, Rc, a.n), num = 0.0;
   den = block_sum(den, red);
   if (anti) {
-    for (int i = threadIdx.x; i < a.n; i += blockDim.x) num += (double)fl[i] * Rf[i];
+    num = part_dot(fl, Rf, a.n);
     num = block_sum(num, red);
   }
   if (a.rho_out) {  // symmetrised sampling: the ratio only, decided per pair
@@ -278,10 +318,7 @@ __global__ void dot_kernel(const float* a, long long bsa, const float* bb, long 
                            unsigned* status) {
   __shared__ double red[kThreads / 32];
   const int b = blockIdx.x;
-  const float* x = a + b * bsa;
-  const float* y = bb + b * bsb;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)x[i] * y[i];
+  double s = part_dot(a + b * bsa, bb + b * bsb, n);
   s = block_sum(s, red);
   if (threadIdx.x == 0) {
     out[b] = s;
@@ -298,10 +335,7 @@ __global__ void ratio_accum_kernel(const float* a, long long bsa, const float* b
   const int b = blockIdx.x;
   const int8_t* sp = spins + b * spin_stride;
   if (sp[si] == sp[sj]) return;  // no off-diagonal element for a parallel pair
-  const float* x = a + b * bsa;
-  const float* y = bb + b * bsb;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)x[i] * y[i];
+  double s = part_dot(a + b * bsa, bb + b * bsb, n);
   s = block_sum(s, red);
   if (threadIdx.x == 0) {
     const double r = s / den[b];

@@ -16,6 +16,15 @@ records, per order, the worst and median relative deviation of the sweep ratios 
 to max(|rho|, 1)) and the norm-wise deviation of G, for the cases of tests/test_gpu_parity.py:
 bond-decay 8x8 sweeps and the oracle-sampled iid 8x8 configurations.  The GPU tests bound
 their float32 results by twice the largest value over the orders.
+
+Split BF16 (tests/test_gpu_mixed.py, tests/test_gpu_parity_24x24.py): every pairwise
+product of every einsum takes its two operands as BF16 hi + lo and accumulates in
+float32, the QR stays float32 Householder, in the same six rounding orders; recorded are
+the worst sweep-ratio deviation, E_loc relative to its term scale, ln|Psi|, and G
+norm-wise and element-wise, over the orders and the cases' chains (8x8: six chains, one
+sweep; 24x24: two chains, the first column of the sweep and a measurement).  A ratio
+whose contraction nearly cancels can move by ~1e-3 with the QR's summation order alone,
+which is why one order is not enough.  ``--split-only`` recomputes only these figures.
 """
 import json
 import os
@@ -143,22 +152,33 @@ def split_einsum(spec, *ops):
 
 
 class SplitOracle:
-    """Context manager: the oracle's einsums in emulated split BF16, the QR in float32."""
+    """Context manager: the oracle's einsums in emulated split BF16, the QR in float32,
+    in one of the six rounding orders (QR dot-product order x contraction order)."""
+
+    def __init__(self, order=("dot", "oracle")):
+        self.dots, self.path = order
 
     def __enter__(self):
         self.saved = (vmc._einsum, vmc.qr_pos, vmc.np.einsum)
         npe = self.saved[2]
-        vmc._einsum = split_einsum
+        if self.path == "oracle":
+            vmc._einsum = split_einsum
+        else:
+            def rev(spec, *ops):
+                ins, out = spec.split("->")
+                return split_einsum(",".join(ins.split(",")[::-1]) + "->" + out, *ops[::-1])
+            vmc._einsum = rev
         vmc.np.einsum = lambda spec, *ops, **kw: npe(spec, *[np.asarray(o, F32) for o in ops], **kw).astype(F32)
-        vmc.qr_pos = lambda M: householder32(M, "dot")
+        vmc.qr_pos = lambda M: householder32(M, self.dots)
         return self
 
     def __exit__(self, *a):
         vmc._einsum, vmc.qr_pos, vmc.np.einsum = self.saved
 
 
-def split_spread(w, start, seed, t, chains, first_column_only=False):
-    """Sweep-ratio and measurement deviations of emulated split BF16 from float64."""
+def split_spread(w, start, seed, t, chains, first_column_only=False, order=("dot", "oracle")):
+    """Sweep-ratio and measurement deviations of emulated split BF16 from float64, in one
+    rounding order."""
     g = vmc.unpack(w["tensors"], w["Ly"], w["Lx"], w["D"])
     g32 = [[x.astype(F32) for x in row] for row in g]
     W, W32 = w["sketch"], w["sketch"].astype(F32)
@@ -178,7 +198,7 @@ def split_spread(w, start, seed, t, chains, first_column_only=False):
             first_column(g, start[c], W, ref)
         else:
             vmc.sweep(g, start[c], w["chi"], W, 3, seed, c, t, trace=ref)
-        with SplitOracle():
+        with SplitOracle(order):
             tr = vmc.Trace(follow={b: int(a) for b, _, _, a in ref.rows}, tie=1e-5)
             if first_column_only:
                 first_column(g32, start[c], W32, tr)
@@ -187,14 +207,14 @@ def split_spread(w, start, seed, t, chains, first_column_only=False):
         r64 = {b: rho for b, rho, _, _ in ref.rows}
         ratio_dev += [abs(rho - r64[b]) / max(abs(r64[b]), 1.0) for b, rho, _, _ in tr.rows]
         m64 = vmc.measure(g, start[c], w["chi"], W, 3, w["J1"], w["J2"])
-        with SplitOracle():
+        with SplitOracle(order):
             m32 = vmc.measure(g32, start[c], w["chi"], W32, 3, w["J1"], w["J2"])
         eloc_dev.append(abs(m32["eloc"] - m64["eloc"]) / m64["eloc_scale"])
         lp_dev.append(abs(m32["logpsi"] - m64["logpsi"]))
         G64, G32 = flat(m64["G"]), flat(m32["G"]).astype(np.float64)
         g_nrm.append(np.linalg.norm(G32 - G64) / np.linalg.norm(G64))
         g_el.append(np.max(np.abs(G32 - G64)) / np.max(np.abs(G64)))
-        print("split", w["Ly"], c, max(ratio_dev), eloc_dev[-1], lp_dev[-1], g_nrm[-1], g_el[-1], flush=True)
+        print("split", w["Ly"], order, c, max(ratio_dev), eloc_dev[-1], lp_dev[-1], g_nrm[-1], g_el[-1], flush=True)
     out["sweep_ratio_max"] = float(np.max(ratio_dev))
     out["sweep_ratio_median"] = float(np.median(ratio_dev))
     out["eloc_rel_scale_max"] = float(np.max(eloc_dev))
@@ -242,6 +262,26 @@ def grad_spread(w, configs):
     return out
 
 
+def _split_case(args):
+    name, order = args
+    if name == "8x8":
+        w = inputs.workload("peps_8x8", n_chains=6)
+        w["tensors"] = inputs.peps_tensors(8, 8, 4, w["seed"], True, bond_decay=1.0)
+        return split_spread(w, inputs.start_spins(6, 8, 8, 31, "random"), 11, 3, range(6), order=order)
+    w = inputs.workload("peps_24x24", n_chains=2)
+    w["tensors"] = inputs.peps_tensors(24, 24, 8, w["seed"], False, bond_decay=1.0)
+    return split_spread(w, inputs.start_spins(2, 24, 24, w["seed"], "random"), w["seed"], 7, range(2),
+                        first_column_only=True, order=order)
+
+
+def split_over_orders(name, pool):
+    """Worst (and worst median) over the six rounding orders of each split-BF16 figure."""
+    per = pool.map(_split_case, [(name, o) for o in ORDERS])
+    out = {k: float(max(r[k] for r in per)) for k in per[0]}
+    out["per_order"] = {"%s/%s" % o: r for o, r in zip(ORDERS, per)}
+    return out
+
+
 def summary(per_order):
     vals = list(per_order.values())
     if isinstance(vals[0], dict):
@@ -251,8 +291,15 @@ def summary(per_order):
 
 
 def main():
-    res = {"how": "tests/golden/make_float32_spread.py: the oracle in float32 (plain Householder QR) in "
-                  "3 dot-product orders x 2 contraction orders against the float64 oracle"}
+    if "--split-only" in sys.argv[1:]:   # keep the float32 figures, recompute the split-BF16 ones
+        with open(os.path.join(HERE, "float32_spread.json")) as f:
+            res = json.load(f)
+        _split_into(res)
+        _write(res)
+        return
+    res = {"how": "tests/golden/make_float32_spread.py: the oracle in float32 (plain Householder QR) and in "
+                  "emulated split BF16, each in 3 dot-product orders x 2 contraction orders, against the "
+                  "float64 oracle"}
     w = inputs.workload("peps_8x8", n_chains=6)
     w["tensors"] = inputs.peps_tensors(8, 8, 4, w["seed"], True, bond_decay=1.0)
     res["sweep_ratios_bond_decay_8x8"] = summary(
@@ -261,13 +308,21 @@ def main():
     sampled = golden.load("peps_8x8")
     res["sweep_ratios_iid_8x8_sampled"] = summary(sweep_spread(w, sampled, 77, 12, (0, 3, 5, 7)))
     res["grad_iid_8x8_sampled"] = summary(grad_spread(w, sampled))
-    w = inputs.workload("peps_8x8", n_chains=6)
-    w["tensors"] = inputs.peps_tensors(8, 8, 4, w["seed"], True, bond_decay=1.0)
-    res["split_bf16_bond_decay_8x8"] = split_spread(w, inputs.start_spins(6, 8, 8, 31, "random"), 11, 3, range(6))
-    w = inputs.workload("peps_24x24", n_chains=2)
-    w["tensors"] = inputs.peps_tensors(24, 24, 8, w["seed"], False, bond_decay=1.0)
-    res["split_bf16_bond_decay_24x24"] = split_spread(w, inputs.start_spins(2, 24, 24, w["seed"], "random"),
-                                                      w["seed"], 7, range(2), first_column_only=True)
+    _split_into(res)
+    _write(res)
+
+
+def _split_into(res):
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(len(ORDERS)) as pool:
+        res["split_bf16_bond_decay_8x8"] = split_over_orders("8x8", pool)
+        res["split_bf16_bond_decay_24x24"] = split_over_orders("24x24", pool)
+    res["how"] = ("tests/golden/make_float32_spread.py: the oracle in float32 (plain Householder QR) and in "
+                  "emulated split BF16, each in 3 dot-product orders x 2 contraction orders, against the "
+                  "float64 oracle")
+
+
+def _write(res):
     with open(os.path.join(HERE, "float32_spread.json"), "w") as f:
         json.dump(res, f, indent=1)
         f.write("\n")

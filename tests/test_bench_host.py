@@ -27,10 +27,15 @@ def test_kernel_groups_totals():
     shapes = [{"shape": "fused4 32 32 32 32", "launches": 2, "flops": 4.0, "ms": 1.0},
               {"shape": "fused4 8 8 32 32", "launches": 1, "flops": 1.0, "ms": 0.5},
               {"shape": "gemm tc M256 N32 K256", "launches": 3, "flops": 3.0, "ms": 0.3},
-              {"shape": "qr 256x32", "launches": 5, "flops": 0.0, "ms": 0.2}]
+              {"shape": "qr 256x32", "launches": 5, "flops": 0.0, "ms": 0.2},
+              {"shape": "fusedP 32 32 32 32 x 8 8 8 8", "launches": 4, "flops": 8.0, "ms": 0.4},
+              {"shape": "metropolis", "launches": 6, "flops": 0.0, "ms": 0.1},
+              {"shape": "normalize_pow2", "launches": 2, "flops": 0.0, "ms": 0.05}]
     g = bench.kernel_groups(shapes)
     assert g["fused4"] == {"launches": 3, "flops": 5.0, "ms": 1.5}
     assert g["gemm_tc"]["launches"] == 3 and g["qr"]["ms"] == 0.2
+    assert g["fusedP"]["launches"] == 4 and g["reductions"]["launches"] == 8
+    assert abs(g["reductions"]["ms"] - 0.15) < 1e-12
 
 
 def test_default_arguments():
@@ -44,3 +49,16 @@ def test_traffic_records_name_their_sources_and_summaries():
         assert os.path.exists(os.path.join(bench.ROOT, t["source"]))
         assert os.path.exists(os.path.join(bench.ROOT, t["summary"]))
         assert len(bench.source_sha(t["source"])) == 16 and t["bytes_per_chain"] > 0
+
+
+def test_binding_roof_follows_the_ridge_point():
+    """A kernel whose algorithmic intensity lies below the ridge point (compute peak over
+    HBM bandwidth) is reported against HBM, one above it against the compute peak."""
+    import bench
+    cpeak, hbm = (("tensor", 1714.6, "m"), (6781.4, "m"))
+    ridge = 1714.6e12 / 6781.4e9
+    lo, other, inten, r = bench.binding_roofline(128.0 * 1e6, 1e6, 1e-3, cpeak, hbm)
+    assert r == ridge and inten == 128.0 and lo["bound"] == "hbm" and other["bound"] == "tensor"
+    assert abs(lo["achieved"] - 1.0) < 1e-12 and abs(lo["frac"] - 1.0 / 6781.4) < 1e-15
+    hi, other, _, _ = bench.binding_roofline(400.0 * 1e6, 1e6, 1e-3, cpeak, hbm)
+    assert hi["bound"] == "tensor" and abs(hi["achieved"] - 0.4) < 1e-12 and other["bound"] == "hbm"

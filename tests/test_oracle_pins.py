@@ -177,6 +177,42 @@ def test_fit_between_optimal_bound_and_tt_svd():
     assert errs[2] <= errs[0] + 1e-12
 
 
+def test_svd_truncation_is_right_to_left_tt_svd():
+    """The SVD truncation mode (App. B's truncation done by SVD instead of the fit) equals
+    textbook TT-SVD of the dense vector run from the right end, its output is
+    left-orthonormal and normalised, and at Dc >= the exact bonds it reproduces X."""
+    rng = np.random.default_rng(6)
+    L, p, chiX, chi = 6, 2, 6, 3
+    X = [rng.standard_normal((1 if m == 0 else chiX, p, 1 if m == L - 1 else chiX)) for m in range(L)]
+    x = _dense(X)
+    r = vmc.bond_caps([chiX] * (L - 1), [p] * L, chi)
+    V, ln = vmc.compress_svd(X, chi)
+    v = _dense(V) * np.exp(ln)
+    xr = x.reshape((p,) * L).transpose(tuple(range(L - 1, -1, -1))).reshape(-1)
+    tt = _dense(_svd_truncate_dense(xr, [p] * L, r[::-1]))
+    ref = tt.reshape((p,) * L).transpose(tuple(range(L - 1, -1, -1))).reshape(-1)
+    assert np.linalg.norm(v - ref) <= 1e-10 * np.linalg.norm(ref)
+    for t in V[:-1]:
+        M = t.reshape(-1, t.shape[2])
+        assert np.allclose(M.T @ M, np.eye(M.shape[1]), atol=1e-12)
+    assert np.linalg.norm(V[-1]) == pytest.approx(1.0, rel=1e-14)
+    V, ln = vmc.compress(X, 64, None, 0)
+    assert np.linalg.norm(_dense(V) * np.exp(ln) - x) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_svd_mode_boundary_mps_exact_at_full_dc():
+    """Both truncation modes give the exact amplitude through the whole contraction once
+    Dc >= D^(L/2) (4x4, D = 2, Dc = 4), and agree with each other there."""
+    g = peps(4, 4, 2, 12)
+    W = sk(4, 4, 2)
+    for seed in range(3):
+        c = rand_cfg(4, 4, seed)
+        ref = exact.amplitude_transfer(g, c)
+        for n_fit in (0, 1):
+            r = vmc.measure(g, c, 4, W, n_fit, 1.0, 0.5, want_grad=False)
+            assert r["sign"] * np.exp(r["logpsi"]) == pytest.approx(ref, rel=1e-10)
+
+
 def test_fit_output_left_orthonormal_and_normalised():
     rng = np.random.default_rng(2)
     X = [rng.standard_normal((1 if m == 0 else 8, 3, 1 if m == 4 else 8)) for m in range(5)]
