@@ -51,8 +51,8 @@ NCU_TRAFFIC = {
     "fused4": {"bytes_per_chain": (167.906304e6 + 91.586304e6) / 512,
                "source": "paper_1908_09359_gb300/csrc/fused_env4.cu", "source_sha": "2cb0277a6c9307e6",
                "summary": "profiles/fused4_env4_bulk_peps24x24.md"},
-    "fused3": {"bytes_per_chain": (201.427456e6 + 45.492992e6) / 2048,
-               "source": "paper_1908_09359_gb300/csrc/fused_env3.cu", "source_sha": "1b8d8fc64503cdc2",
+    "fused3": {"bytes_per_chain": (201.532416e6 + 45.497088e6) / 2048,
+               "source": "paper_1908_09359_gb300/csrc/fused_env3.cu", "source_sha": "49d7a78cd75df968",
                "summary": "profiles/fused3_env3_bulk_peps24x24.md"},
 }
 

@@ -323,6 +323,21 @@ int pepsvmc_env3_left_noalloc(const float* E, const float* T, const float* A,
                               int32_t cB2, int32_t Dl, int32_t Dr, int32_t Du, int32_t Dd,
                               void* stream);
 
+/* Batched thin QR with a non-negative diagonal of R, the factorisation the
+ * variational fit of App. B uses to move the orthogonality centre (Householder
+ * reflections in float32; no context, no allocation).  Y, Q: device float32, `batch`
+ * matrices of rows x cols stored one after another (rows * cols floats each),
+ * row-major (element (i,j) at i*cols + j) or, with col_major != 0, column-major (at
+ * j*rows + i); Q may equal Y (in place), otherwise the two must not overlap.  Q is the
+ * unique thin factor with R(j,j) > 0 for full-rank input; a column that is zero after
+ * the previous reflections gets no reflector (R(j,j) = 0) and Q keeps the identity's
+ * column there, transformed by the other reflectors.  Asynchronous on ``stream`` (a
+ * cudaStream_t, NULL = legacy default stream), current device.
+ * Errors: EINVAL for null pointers, batch < 1, cols < 1, cols > 64 or rows < cols;
+ * ECUDA.                                                                          */
+int pepsvmc_qr_pos(const float* Y, float* Q, int32_t batch, int32_t rows, int32_t cols,
+                   int32_t col_major, void* stream);
+
 /* ------------------------------------------------------------- learned proposal
  * Exact Metropolis-Hastings moves proposed by a small convolutional network (no
  * counterpart in the paper's Sec. II sampler; it uses the MH form of Eq. (8) with a

@@ -34,7 +34,7 @@ SYMBOLS = [
     "pepsvmc_proposal_logits", "pepsvmc_proposal_collect", "pepsvmc_proposal_dataset_size", "pepsvmc_proposal_load",
     "pepsvmc_proposal_train", "pepsvmc_train_proposal", "pepsvmc_set_proposal", "pepsvmc_learned_sweep", "pepsvmc_get_learned_trace",
     "pepsvmc_env4_left", "pepsvmc_set_fused", "pepsvmc_random_sweep", "pepsvmc_get_random_trace", "pepsvmc_set_wait_budget", "pepsvmc_get_sums", "pepsvmc_set_sums", "pepsvmc_sums_device", "pepsvmc_finalize_sums",
-    "pepsvmc_get_phi", "pepsvmc_simple_update",
+    "pepsvmc_get_phi", "pepsvmc_simple_update", "pepsvmc_qr_pos",
 ]
 
 
@@ -92,6 +92,7 @@ def load(path: str | None = None):
         "pepsvmc_get_profile": (C.c_int, [P, D]),
         "pepsvmc_env3_left": (C.c_int, [P, P, P, P, P, P, P] + [I32] * 9),
         "pepsvmc_env3_left_noalloc": (C.c_int, [P, P, P, P, P, P] + [I32] * 9 + [P]),
+        "pepsvmc_qr_pos": (C.c_int, [P, P, I32, I32, I32, I32, P]),
         "pepsvmc_get_profile_shapes": (C.c_int, [P, C.c_char_p, I64]),
         "pepsvmc_set_autotune": (C.c_int, [P, I32]),
         "pepsvmc_set_contraction_kernel": (C.c_int, [P, I32, I32]),

@@ -347,6 +347,23 @@ def env3_left_noalloc(E, T, A, spins, B, out, dims, stream=None):
                                "null pointers or a CUDA error)")
 
 
+def qr_pos(Y, Q, col_major=False, stream=None):
+    """Batched thin QR with diag(R) > 0 (pepsvmc_qr_pos) of the float32 CUDA tensor Y
+    (batch, rows, cols) into Q (same shape; may be Y itself).  Y and Q hold each matrix
+    row-major, or column-major with col_major (then the tensors' last two dimensions are
+    read as (cols, rows))."""
+    lib = _lib.load()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    batch = Y.shape[0]
+    rows, cols = (Y.shape[2], Y.shape[1]) if col_major else (Y.shape[1], Y.shape[2])
+    rc = lib.pepsvmc_qr_pos(C.c_void_p(Y.data_ptr()), C.c_void_p(Q.data_ptr()), int(batch), int(rows), int(cols),
+                            int(bool(col_major)), C.c_void_p(stream))
+    if rc != 0:
+        raise PepsvmcError(rc, "pepsvmc_qr_pos failed (invalid sizes, null pointers or a CUDA error)")
+
+
 def simple_update(Ly, Lx, D, B, lam_h, lam_v, J1=1.0, J2=0.0, tau=0.01, max_steps=100, tol=1e-11, stream=None):
     """Simple-update imaginary-time evolution (pepsvmc_simple_update) from the packed site
     tensors B and link vectors lam_h (Ly, Lx-1, D), lam_v (Ly-1, Lx, D).  Returns

@@ -56,20 +56,40 @@ __device__ __forceinline__ float block_max(float v, float* red) {
 __device__ __forceinline__ bool vec4_ok(const void* x, const void* y, int n) {
   return (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) == 0) && (n & 3) == 0;
 }
-// this thread's part of sum_i x[i] y[i] in float64
+// One step of Dot2 (Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26, 2005): the product is split exactly into p + e (TwoProduct with a fused
+// multiply-add), p is added to the running sum hi with Knuth's TwoSum, and both rounding
+// errors go to lo.  hi + lo then carries about twice float32's precision -- as accurate
+// as float64 accumulation of the exact products, which matters where the sum cancels
+// (amplitude closures, ratios), without float64 arithmetic, which runs at a small
+// fraction of the float32 rate on this GPU.  The _rn intrinsics are never contracted
+// into fused multiply-adds, so each transformation stays error-free.
+__device__ __forceinline__ void dot2_step(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bv = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+// this thread's part of sum_i x[i] y[i] (Dot2 in float32 pairs, returned in float64)
 __device__ __forceinline__ double part_dot(const float* x, const float* y, int n) {
-  double s = 0.0;
+  float hi = 0.f, lo = 0.f;
   if (vec4_ok(x, y, n)) {
     const float4* x4 = reinterpret_cast<const float4*>(x);
     const float4* y4 = reinterpret_cast<const float4*>(y);
     for (int i = threadIdx.x; i < (n >> 2); i += blockDim.x) {
       const float4 a = x4[i], b = y4[i];
-      s += (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
+      dot2_step(hi, lo, a.x, b.x);
+      dot2_step(hi, lo, a.y, b.y);
+      dot2_step(hi, lo, a.z, b.z);
+      dot2_step(hi, lo, a.w, b.w);
     }
   } else {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)x[i] * y[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dot2_step(hi, lo, x[i], y[i]);
   }
-  return s;
+  return (double)hi + (double)lo;
 }
 // this thread's part of max |x[i]|; *bad set when an entry is not finite
 __device__ __forceinline__ float part_maxabs(const float* x, int n, bool* bad) {

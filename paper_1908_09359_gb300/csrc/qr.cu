@@ -11,6 +11,7 @@
 // (below) is used instead.  Reflector j: v = x + sign(x0)|x| e1, beta = 2/(v.v);
 // a zero column gets no reflector and a zero diagonal.
 #include "common.cuh"
+#include "pepsvmc.h"
 
 namespace pv {
 namespace {
@@ -246,3 +247,13 @@ cudaError_t qr_pos_batched(const float* Y, long long bsY, long long yrs, long lo
 }
 
 }  // namespace pv
+
+extern "C" int pepsvmc_qr_pos(const float* Y, float* Q, int32_t batch, int32_t rows, int32_t cols, int32_t col_major,
+                              void* stream) {
+  if (!Y || !Q || batch < 1 || cols < 1 || cols > 64 || rows < cols) return PEPSVMC_EINVAL;
+  const long long bs = (long long)rows * cols;
+  const long long rs = col_major ? 1 : cols, cs = col_major ? rows : 1;
+  const cudaError_t e =
+      pv::qr_pos_batched(Y, bs, rs, cs, Q, bs, rs, cs, rows, cols, batch, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PEPSVMC_OK : PEPSVMC_ECUDA;
+}
