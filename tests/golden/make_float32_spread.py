@@ -22,9 +22,12 @@ product of every einsum takes its two operands as BF16 hi + lo and accumulates i
 float32, the QR stays float32 Householder, in the same six rounding orders; recorded are
 the worst sweep-ratio deviation, E_loc relative to its term scale, ln|Psi|, and G
 norm-wise and element-wise, over the orders and the cases' chains (8x8: six chains, one
-sweep; 24x24: two chains, the first column of the sweep and a measurement).  A ratio
+sweep and a measurement each; 24x24: the chains tests/test_gpu_parity_24x24.py checks in
+the 512-chain launch -- the first column of the sweep of chains 0 and 341 and the
+measurement of the start configurations of chains 85 and 426).  A ratio
 whose contraction nearly cancels can move by ~1e-3 with the QR's summation order alone,
-which is why one order is not enough.  ``--split-only`` recomputes only these figures.
+which is why one order is not enough.  ``--split-only`` recomputes only these figures,
+``--split24-only`` only the 24x24 ones.
 """
 import json
 import os
@@ -43,6 +46,10 @@ import make_sampled_configs as golden  # noqa: E402
 
 F32 = np.float32
 ORDERS = [(dots, path) for path in ("oracle", "reversed") for dots in ("dot", "seq", "rev")]
+# chains of the 512-chain 24x24 launch whose first-column sweep and start-configuration
+# measurement tests/test_gpu_parity_24x24.py compares with the float64 oracle
+SWEEP_CHAINS_24 = (0, 341)
+MEASURE_CHAINS_24 = (85, 426)
 
 
 def householder32(M, order):
@@ -176,9 +183,11 @@ class SplitOracle:
         vmc._einsum, vmc.qr_pos, vmc.np.einsum = self.saved
 
 
-def split_spread(w, start, seed, t, chains, first_column_only=False, order=("dot", "oracle")):
+def split_spread(w, start, seed, t, chains, first_column_only=False, order=("dot", "oracle"),
+                 measure_chains=None):
     """Sweep-ratio and measurement deviations of emulated split BF16 from float64, in one
-    rounding order."""
+    rounding order: the sweep (or its first column) of every chain in ``chains`` and the
+    measurement of ``start[c]`` for every c in ``measure_chains`` (default: ``chains``)."""
     g = vmc.unpack(w["tensors"], w["Ly"], w["Lx"], w["D"])
     g32 = [[x.astype(F32) for x in row] for row in g]
     W, W32 = w["sketch"], w["sketch"].astype(F32)
@@ -206,6 +215,8 @@ def split_spread(w, start, seed, t, chains, first_column_only=False, order=("dot
                 vmc.sweep(g32, start[c], w["chi"], W32, 3, seed, c, t, trace=tr)
         r64 = {b: rho for b, rho, _, _ in ref.rows}
         ratio_dev += [abs(rho - r64[b]) / max(abs(r64[b]), 1.0) for b, rho, _, _ in tr.rows]
+        print("split sweep", w["Ly"], order, c, max(ratio_dev), flush=True)
+    for c in (chains if measure_chains is None else measure_chains):
         m64 = vmc.measure(g, start[c], w["chi"], W, 3, w["J1"], w["J2"])
         with SplitOracle(order):
             m32 = vmc.measure(g32, start[c], w["chi"], W32, 3, w["J1"], w["J2"])
@@ -214,7 +225,7 @@ def split_spread(w, start, seed, t, chains, first_column_only=False, order=("dot
         G64, G32 = flat(m64["G"]), flat(m32["G"]).astype(np.float64)
         g_nrm.append(np.linalg.norm(G32 - G64) / np.linalg.norm(G64))
         g_el.append(np.max(np.abs(G32 - G64)) / np.max(np.abs(G64)))
-        print("split", w["Ly"], order, c, max(ratio_dev), eloc_dev[-1], lp_dev[-1], g_nrm[-1], g_el[-1], flush=True)
+        print("split measure", w["Ly"], order, c, eloc_dev[-1], lp_dev[-1], g_nrm[-1], g_el[-1], flush=True)
     out["sweep_ratio_max"] = float(np.max(ratio_dev))
     out["sweep_ratio_median"] = float(np.median(ratio_dev))
     out["eloc_rel_scale_max"] = float(np.max(eloc_dev))
@@ -268,10 +279,11 @@ def _split_case(args):
         w = inputs.workload("peps_8x8", n_chains=6)
         w["tensors"] = inputs.peps_tensors(8, 8, 4, w["seed"], True, bond_decay=1.0)
         return split_spread(w, inputs.start_spins(6, 8, 8, 31, "random"), 11, 3, range(6), order=order)
-    w = inputs.workload("peps_24x24", n_chains=2)
+    # the chains and start configurations that tests/test_gpu_parity_24x24.py checks
+    w = inputs.workload("peps_24x24", n_chains=512)
     w["tensors"] = inputs.peps_tensors(24, 24, 8, w["seed"], False, bond_decay=1.0)
-    return split_spread(w, inputs.start_spins(2, 24, 24, w["seed"], "random"), w["seed"], 7, range(2),
-                        first_column_only=True, order=order)
+    return split_spread(w, inputs.start_spins(512, 24, 24, w["seed"], "random"), w["seed"], 7, SWEEP_CHAINS_24,
+                        first_column_only=True, order=order, measure_chains=MEASURE_CHAINS_24)
 
 
 def split_over_orders(name, pool):
@@ -291,10 +303,11 @@ def summary(per_order):
 
 
 def main():
-    if "--split-only" in sys.argv[1:]:   # keep the float32 figures, recompute the split-BF16 ones
+    if "--split-only" in sys.argv[1:] or "--split24-only" in sys.argv[1:]:
+        # keep the float32 figures (and with --split24-only the 8x8 split ones), recompute the rest
         with open(os.path.join(HERE, "float32_spread.json")) as f:
             res = json.load(f)
-        _split_into(res)
+        _split_into(res, only24="--split24-only" in sys.argv[1:])
         _write(res)
         return
     res = {"how": "tests/golden/make_float32_spread.py: the oracle in float32 (plain Householder QR) and in "
@@ -312,10 +325,11 @@ def main():
     _write(res)
 
 
-def _split_into(res):
+def _split_into(res, only24=False):
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(len(ORDERS)) as pool:
-        res["split_bf16_bond_decay_8x8"] = split_over_orders("8x8", pool)
+        if not only24:
+            res["split_bf16_bond_decay_8x8"] = split_over_orders("8x8", pool)
         res["split_bf16_bond_decay_24x24"] = split_over_orders("24x24", pool)
     res["how"] = ("tests/golden/make_float32_spread.py: the oracle in float32 (plain Householder QR) and in "
                   "emulated split BF16, each in 3 dot-product orders x 2 contraction orders, against the "

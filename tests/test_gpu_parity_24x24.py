@@ -10,10 +10,11 @@ moves ln|Psi| by 0.1-0.9 after a few sweeps), so there only the throughput is me
 Checked: for two chains, every ratio and decision of the sweep's first column (the
 oracle replays the transposed lattice's first row with its bottom environments, taking
 the GPU's decision at near-ties |ln r - ln rho^2| < 1e-5; a whole oracle sweep of this
-lattice takes over ten minutes of host time); for four chains, E_loc, ln|Psi|, sign and G
-of the measurement after the sweep.  Bounds: twice the deviation of the oracle itself run
-in emulated split BF16 at these shapes (tests/golden/float32_spread.json, written by
-tests/golden/make_float32_spread.py).  The oracle runs in six spawned single-threaded
+lattice takes over ten minutes of host time); for two other chains, E_loc, ln|Psi|, sign
+and G of the measurement of their start configurations.  Bounds: twice the worst
+deviation of the oracle itself, run in emulated split BF16 in six rounding orders on
+these same chains and configurations (tests/golden/float32_spread.json, written by
+tests/golden/make_float32_spread.py).  The oracle runs in spawned single-threaded
 processes.
 """
 import json
@@ -26,8 +27,8 @@ from paper_1908_09359_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-SWEEP_CHAINS = (0, 341)
-MEASURE_CHAINS = (85, 170, 426, 511)
+SWEEP_CHAINS = (0, 341)     # the chains the bounds were derived on
+MEASURE_CHAINS = (85, 426)
 SPLIT = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
                                     "float32_spread.json")))["split_bf16_bond_decay_24x24"]
 
@@ -75,17 +76,17 @@ def test_bench_launch_matches_oracle_on_sampled_chains():
     ctx.set_spins(start)
     ctx.energy_and_grad(2, want_samples=False, want_grad=False)  # autotuner, sketches, graph capture + replay
     ctx.set_spins(start)
+    e, lp, sg = ctx.measure()
+    G = {c: ctx.chain_grad(c) for c in MEASURE_CHAINS}
+    ctx.set_spins(start)
     ctx.set_sweep_counter(7)
     ctx.enable_trace(True)
     ctx.sample_sweep(1)
     ratio, dec = ctx.get_trace()
-    final = ctx.get_spins()
-    e, lp, sg = ctx.measure()
-    G = {c: ctx.chain_grad(c) for c in MEASURE_CHAINS}
     ctx.close()
     col0 = set(range(23))  # vertical bonds of column 0 (ids m*(Ly-1)+k with m = 0)
     jobs = [("sweep", c, start[c], {b: int(dec[c, b]) for b in col0 if dec[c, b] >= 0}) for c in SWEEP_CHAINS]
-    jobs += [("measure", c, final[c], None) for c in MEASURE_CHAINS]
+    jobs += [("measure", c, start[c], None) for c in MEASURE_CHAINS]
     with mp.get_context("spawn").Pool(len(jobs), initializer=_one_thread) as pool:
         res = pool.map(_oracle_job, jobs)
     rtol = 2 * SPLIT["sweep_ratio_max"]
