@@ -140,14 +140,32 @@ __global__ void gather_kernel(float* dst, const double* src, const int* map, lon
     dst[i] = (float)src[map[i]];
 }
 
-// Scale x (and x2, x3 by the same factor) by 2^-e, e the exponent of max|x|.
+// Scale x (and x2, x3 by the same factor) by 2^-e, e the exponent of max|x|.  Up to
+// kNormRegF4 * 4 * kThreads elements (every three-line environment of Dc <= 32, D <= 8)
+// are read once into registers and written back scaled; larger arrays take a second
+// pass.
+constexpr int kNormRegF4 = 8;
 __global__ void normalize_pow2_kernel(float* x, long long bs, int n, float* x2, long long bs2, int n2, float* x3,
                                       long long bs3, int n3, int* exps, unsigned* status) {
   __shared__ float red[kThreads / 32];
   const int b = blockIdx.x;
   float* xb = x + b * bs;
   bool bad = false;
-  float mx = part_maxabs(xb, n, &bad);
+  const bool in_regs = vec4_ok(xb, xb, n) && n <= kNormRegF4 * 4 * kThreads;
+  float4 r[kNormRegF4];
+  float mx = 0.f;
+  if (in_regs) {
+    const float4* x4 = reinterpret_cast<const float4*>(xb);
+#pragma unroll
+    for (int i = 0; i < kNormRegF4; ++i) {
+      const int j = threadIdx.x + i * kThreads;
+      r[i] = j < (n >> 2) ? x4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+      bad |= !isfinite(r[i].x) || !isfinite(r[i].y) || !isfinite(r[i].z) || !isfinite(r[i].w);
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(r[i].x), fabsf(r[i].y)), fmaxf(fabsf(r[i].z), fabsf(r[i].w))));
+    }
+  } else {
+    mx = part_maxabs(xb, n, &bad);
+  }
   if (__syncthreads_or(bad)) {
     if (threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
     return;
@@ -160,7 +178,16 @@ __global__ void normalize_pow2_kernel(float* x, long long bs, int n, float* x2, 
   int e;
   frexpf(mx, &e);
   const float s = ldexpf(1.f, -e);
-  scale_copy(xb, xb, n, s);
+  if (in_regs) {
+    float4* x4 = reinterpret_cast<float4*>(xb);
+#pragma unroll
+    for (int i = 0; i < kNormRegF4; ++i) {
+      const int j = threadIdx.x + i * kThreads;
+      if (j < (n >> 2)) x4[j] = make_float4(r[i].x * s, r[i].y * s, r[i].z * s, r[i].w * s);
+    }
+  } else {
+    scale_copy(xb, xb, n, s);
+  }
   if (x2) scale_copy(x2 + b * bs2, x2 + b * bs2, n2, s);
   if (x3) scale_copy(x3 + b * bs3, x3 + b * bs3, n3, s);
   if (exps && threadIdx.x == 0) exps[b] += e;

@@ -126,34 +126,39 @@ __device__ __forceinline__ float warp_transpose_sum32(float (&p)[kQrRegCols]) {
   return p[0];
 }
 
-// Sum over the block (NT threads) of p[k] for every k into tot_s[k] (shared); red:
-// NT/32 x 32 floats.
+// Sum over the block (NT threads) of p[k] for every k: returns, in lane l of every warp,
+// the block sum of column l (the eight warp sums added in warp order, so every warp
+// holds the same value); red: NT/32 x 32 floats, written before and read after the one
+// barrier.  Consecutive calls must alternate between two red buffers (a warp may still
+// be reading one when another warp writes the next).
 template <int NT>
-__device__ __forceinline__ void block_sum32(float (&p)[kQrRegCols], float* red, float* tot_s) {
+__device__ __forceinline__ float block_sum32(float (&p)[kQrRegCols], float* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float v = warp_transpose_sum32(p);
   red[warp * 32 + lane] = v;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    float s = 0.f;
+  float s = 0.f;
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) s += red[w * 32 + threadIdx.x];
-    tot_s[threadIdx.x] = s;
-  }
-  __syncthreads();
+  for (int w = 0; w < NT / 32; ++w) s += red[w * 32 + lane];
+  return s;
 }
 
 // Y and Q may be the same array (in-place QR): every row is read before any is written.
-// NT threads (64, 128 or 256) hold up to NT rows.
+// NT threads (64, 128 or 256) hold up to NT rows.  One barrier per block reduction: the
+// partial sums are written before it and every thread forms the total after it (in the
+// same order, so all agree bit for bit).  The partials go to two alternating buffers --
+// by the parity of j in the factorisation, where every column passes the norm's barrier,
+// and per reduction done in the Q accumulation, where a zero column has none -- so a
+// buffer is rewritten only after a barrier that follows every read of it.
 template <int NT>
 __global__ void __launch_bounds__(NT) qr_pos_reg_kernel(const float* Y, long long bsY, long long yrs,
                                                                 long long ycs, float* Q, long long bsQ,
                                                                 long long qrs, long long qcs, int R, int C) {
-  __shared__ float red[NT];
-  __shared__ float tot[kQrRegCols];
+  __shared__ float red[2][NT];
+  __shared__ float redn[2][NT / 32];
   __shared__ float beta[kQrRegCols];
   __shared__ int flip[kQrRegCols];
-  __shared__ float x0s[2], nrm;  // x0 by parity of j: a zero column skips the reductions' barriers
+  __shared__ float x0s[2];  // x0 by parity of j: a zero column skips the dot products' barrier
   const int t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5;
   const float* Yb = Y + (long long)blockIdx.x * bsY;
@@ -169,17 +174,13 @@ __global__ void __launch_bounds__(NT) qr_pos_reg_kernel(const float* Y, long lon
     if (j >= C) break;
     float s = (t >= j) ? a[j] * a[j] : 0.f;
     s = warp_sum(s);
-    if (lane == 0) red[warp] = s;
+    if (lane == 0) redn[j & 1][warp] = s;
     if (t == j) x0s[j & 1] = a[j];
     __syncthreads();
-    if (t == 0) {
-      float n2 = 0.f;
+    float n2 = 0.f;
 #pragma unroll
-      for (int w = 0; w < NT / 32; ++w) n2 += red[w];
-      nrm = sqrtf(n2);
-    }
-    __syncthreads();
-    const float alpha = nrm, x0 = x0s[j & 1];
+    for (int w = 0; w < NT / 32; ++w) n2 += redn[j & 1][w];
+    const float alpha = sqrtf(n2), x0 = x0s[j & 1];
     const float sg = (x0 >= 0.f) ? 1.f : -1.f;
     const float bj = alpha == 0.f ? 0.f : 1.f / (alpha * (alpha + fabsf(x0)));
     if (t == 0) {
@@ -191,14 +192,15 @@ __global__ void __launch_bounds__(NT) qr_pos_reg_kernel(const float* Y, long lon
     const float v = (t >= j) ? a[j] : 0.f;
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k) p[k] = (k > j) ? v * a[k] : 0.f;
-    block_sum32<NT>(p, red, tot);
+    const float tot = block_sum32<NT>(p, red[j & 1]);
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k)
-      if (k > j) a[k] = fmaf(-bj * tot[k], v, a[k]);
+      if (k > j) a[k] = fmaf(-bj * __shfl_sync(0xffffffffu, tot, k), v, a[k]);
   }
   __syncthreads();
   // thin Q = H_0 ... H_{C-1} [I; 0], accumulated backwards; H_j touches rows >= j and,
   // at that point, only columns >= j of Q
+  int par = 0;  // alternates per reduction done (a skipped reflector has no barrier)
 #pragma unroll
   for (int j = kQrRegCols - 1; j >= 0; --j) {
     if (j >= C) continue;
@@ -207,10 +209,11 @@ __global__ void __launch_bounds__(NT) qr_pos_reg_kernel(const float* Y, long lon
     const float v = (t >= j) ? a[j] : 0.f;
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k) p[k] = (k >= j) ? v * q[k] : 0.f;
-    block_sum32<NT>(p, red, tot);
+    const float tot = block_sum32<NT>(p, red[par]);
+    par ^= 1;
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k)
-      if (k >= j) q[k] = fmaf(-bj * tot[k], v, q[k]);
+      if (k >= j) q[k] = fmaf(-bj * __shfl_sync(0xffffffffu, tot, k), v, q[k]);
   }
   if (t < R) {
     float* Qb = Q + (long long)blockIdx.x * bsQ;
