@@ -192,10 +192,10 @@ __global__ void __launch_bounds__(NT) qr_pos_reg_kernel(const float* Y, long lon
     const float v = (t >= j) ? a[j] : 0.f;
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k) p[k] = (k > j) ? v * a[k] : 0.f;
-    const float tot = block_sum32<NT>(p, red[j & 1]);
+    const float c = -bj * block_sum32<NT>(p, red[j & 1]);  // lane l: -beta w_l
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k)
-      if (k > j) a[k] = fmaf(-bj * __shfl_sync(0xffffffffu, tot, k), v, a[k]);
+      if (k > j) a[k] = fmaf(__shfl_sync(0xffffffffu, c, k), v, a[k]);
   }
   __syncthreads();
   // thin Q = H_0 ... H_{C-1} [I; 0], accumulated backwards; H_j touches rows >= j and,
@@ -209,11 +209,11 @@ __global__ void __launch_bounds__(NT) qr_pos_reg_kernel(const float* Y, long lon
     const float v = (t >= j) ? a[j] : 0.f;
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k) p[k] = (k >= j) ? v * q[k] : 0.f;
-    const float tot = block_sum32<NT>(p, red[par]);
+    const float c = -bj * block_sum32<NT>(p, red[par]);
     par ^= 1;
 #pragma unroll
     for (int k = 0; k < kQrRegCols; ++k)
-      if (k >= j) q[k] = fmaf(-bj * __shfl_sync(0xffffffffu, tot, k), v, q[k]);
+      if (k >= j) q[k] = fmaf(__shfl_sync(0xffffffffu, c, k), v, q[k]);
   }
   if (t < R) {
     float* Qb = Q + (long long)blockIdx.x * bsQ;
