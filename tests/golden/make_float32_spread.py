@@ -18,8 +18,9 @@ bond-decay 8x8 sweeps and the oracle-sampled iid 8x8 configurations.  The GPU te
 their float32 results by twice the largest value over the orders.
 
 Split BF16 (tests/test_gpu_mixed.py, tests/test_gpu_parity_24x24.py): every pairwise
-product of every einsum takes its two operands as BF16 hi + lo and accumulates in
-float32, the QR stays float32 Householder, in the same six rounding orders; recorded are
+product of every einsum splits both operands into BF16 hi + lo and forms hi.hi + hi.lo +
+lo.hi (the lo.lo product dropped, as the tensor-core form drops it) with float32
+accumulation, the QR stays float32 Householder, in the same six rounding orders; recorded are
 the worst sweep-ratio deviation, E_loc relative to its term scale, ln|Psi|, and G
 norm-wise and element-wise, over the orders and the cases' chains (8x8: six chains, one
 sweep and a measurement each; 24x24: the chains tests/test_gpu_parity_24x24.py checks in
@@ -60,10 +61,9 @@ def householder32(M, order):
     def dot(x, y):
         if order == "dot":
             return F32(np.dot(x, y))
-        s = F32(0)
-        for a, b in (zip(x, y) if order == "seq" else zip(x[::-1], y[::-1])):
-            s = F32(s + a * b)
-        return s
+        # sequential float32 sums of the float32 products (np.cumsum accumulates in order)
+        p = np.multiply(x, y, dtype=F32)
+        return np.cumsum(p if order == "seq" else p[::-1], dtype=F32)[-1] if len(p) else F32(0)
 
     beta, flip = [], []
     for j in range(cols):
@@ -136,9 +136,19 @@ def split_round(x):
     return hi + bf16(x - hi)
 
 
+def split_product(spec, a, b):
+    """One pairwise product as the tensor cores form it in split BF16: both operands split
+    into BF16 hi + lo, the three products hi.hi + hi.lo + lo.hi (lo.lo dropped) each exact
+    in float32 and accumulated in float32."""
+    a, b = np.asarray(a, F32), np.asarray(b, F32)
+    ah, bh = bf16(a), bf16(b)
+    al, bl = bf16(a - ah), bf16(b - bh)
+    return (np.einsum(spec, ah, bh + bl) + np.einsum(spec, al, bh)).astype(F32)
+
+
 def split_einsum(spec, *ops):
-    """The einsum as pairwise products in the oracle's greedy order, each product's two
-    operands rounded to split BF16 and accumulated in float32."""
+    """The einsum as pairwise products in the oracle's greedy order, each product formed
+    as split_product forms it."""
     ins, out = spec.split("->")
     terms = ins.split(",")
     ops = [np.asarray(o, F32) for o in ops]
@@ -152,7 +162,7 @@ def split_einsum(spec, *ops):
         res = "".join(dict.fromkeys(c for c in a + b if c in keep))
         if not rest:
             res = out
-        prod = np.einsum(f"{a},{b}->{res}", split_round(ops[i]), split_round(ops[j])).astype(F32)
+        prod = split_product(f"{a},{b}->{res}", ops[i], ops[j])
         ops = [o for n, o in enumerate(ops) if n not in (i, j)] + [prod]
         terms = rest + [res]
     return np.einsum(f"{terms[0]}->{out}", ops[0]).astype(F32)
@@ -310,9 +320,7 @@ def main():
         _split_into(res, only24="--split24-only" in sys.argv[1:])
         _write(res)
         return
-    res = {"how": "tests/golden/make_float32_spread.py: the oracle in float32 (plain Householder QR) and in "
-                  "emulated split BF16, each in 3 dot-product orders x 2 contraction orders, against the "
-                  "float64 oracle"}
+    res = {"how": HOW}
     w = inputs.workload("peps_8x8", n_chains=6)
     w["tensors"] = inputs.peps_tensors(8, 8, 4, w["seed"], True, bond_decay=1.0)
     res["sweep_ratios_bond_decay_8x8"] = summary(
@@ -331,9 +339,12 @@ def _split_into(res, only24=False):
         if not only24:
             res["split_bf16_bond_decay_8x8"] = split_over_orders("8x8", pool)
         res["split_bf16_bond_decay_24x24"] = split_over_orders("24x24", pool)
-    res["how"] = ("tests/golden/make_float32_spread.py: the oracle in float32 (plain Householder QR) and in "
-                  "emulated split BF16, each in 3 dot-product orders x 2 contraction orders, against the "
-                  "float64 oracle")
+    res["how"] = HOW
+
+
+HOW = ("tests/golden/make_float32_spread.py: the oracle in float32 (plain Householder QR) and in emulated split "
+       "BF16 (hi.hi + hi.lo + lo.hi per pairwise product), each in 3 dot-product orders x 2 contraction orders, "
+       "against the float64 oracle")
 
 
 def _write(res):
